@@ -1,0 +1,159 @@
+/*
+ * bp.h -- exact O(mM) belief propagation on 4-connected grids (C ABI).
+ *
+ * Pairwise MRF (Eq. 1):  P(x) ~ prod_<ij> f(x_i, x_j) prod_i g_i(x_i)
+ * on an H x W 4-connected lattice with M labels per node (the stereo model of
+ * Sec. 6).  The pairwise potential has the sparse compatibility property
+ * (Sec. 1, Sec. 4): f(x_i, x_j) = fbar whenever |x_i - x_j| > T, so a message
+ * update (Eq. 2) is computed exactly in O(mM), m = 2T + 1, as
+ *     m_ij(x_j) = sum_{|x_i - x_j| <= T} [f(x_i, x_j) - fbar] h(x_i) + fbar sum_x h(x)    (Eq. 7)
+ * for sum-product, and for max-product in energies (min-sum) as
+ *     m_ij(x_j) = min{ min_{|x_i - x_j| <= T} [E(x_i - x_j) + h(x_i)], Ebar + min_x h(x) } (Eq. 11)
+ * with h the unary times the other incoming messages (Eq. 5).
+ *
+ * Conventions shared by every call:
+ *  - Arrays passed as `dev_*` are CUDA device pointers on the current device;
+ *    arrays passed as `host_*` are host pointers.  The library never keeps a
+ *    caller pointer after a call returns: inputs are copied into buffers the
+ *    handle owns, outputs are written into caller buffers.
+ *  - Layouts are C order with the label innermost: a unary or belief array is
+ *    [H][W][M]; message planes are [4][H][W][M], where plane s holds the
+ *    message INTO node (r, c) from its neighbour on side s
+ *    (0: left (r, c-1), 1: right (r, c+1), 2: up (r-1, c), 3: down (r+1, c)).
+ *    Slots without a neighbour (grid border) are never read.
+ *  - dtype BP_F32 (sum-product on float32 potentials g, f) or BP_I32
+ *    (min-sum on int32 energies E_u, E).  Energies must lie in [0, 2^26).
+ *  - All device work is ordered on the handle's stream.  Argument and state
+ *    errors are returned synchronously and nothing is launched; device
+ *    errors and kernel time-outs surface at the next call or at bp_sync.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef BPGRID_BP_H
+#define BPGRID_BP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bp_ctx *bp_handle;
+
+typedef enum {
+    BP_OK = 0,
+    BP_ERR_ARG = 1,         /* bad argument (null pointer, size, range)          */
+    BP_ERR_STATE = 2,       /* call out of order (e.g. iterate before set_unary) */
+    BP_ERR_CUDA = 3,        /* a CUDA runtime error; see bp_last_error           */
+    BP_ERR_OOM = 4,         /* device allocation failed                          */
+    BP_ERR_POTENTIAL = 5,   /* max mode with E(d) > Ebar: Eq. 11 needs f >= fbar */
+    BP_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                */
+    BP_ERR_UNSUPPORTED = 7  /* valid request this build cannot serve             */
+} bp_status;
+
+/* Message-passing mode (Sec. 3 and Sec. 5).  BP_LOG and BP_RECORD are flags
+ * or-ed onto BP_SUM: BP_LOG keeps log-messages (numerically robust form of the
+ * same update); BP_RECORD additionally stores checkpoints for bp_backward. */
+typedef enum { BP_SUM = 0, BP_MAX = 1, BP_LOG = 2, BP_RECORD = 4 } bp_mode;
+
+/* Schedules.  BP_SYNC: every message of iteration t+1 from those of
+ * iteration t.  BP_REDBLACK: the checkerboard schedule (Sec. 2, from [2]):
+ * an iteration is a half-step over nodes with (r + c) even, sending all their
+ * messages, then one over nodes with (r + c) odd, in place. */
+typedef enum { BP_SYNC = 0, BP_REDBLACK = 1 } bp_schedule;
+
+typedef enum { BP_F32 = 0, BP_I32 = 1 } bp_dtype;
+
+/* O(M^2) baselines of the standard update (Eq. 2 / Eq. 9), for comparison. */
+typedef enum {
+    BP_DENSE_CUDA_CORE = 0, /* FP32 sum-product or int32 min-sum, CUDA cores          */
+    BP_DENSE_BF16_TC = 1    /* sum-product as a (nodes*4 x M)(M x M) tcgen05 GEMM,    */
+                            /* BF16 operands, FP32 accumulate, normalising epilogue   */
+} bp_dense_kind;
+
+/* Create a handle for an H x W grid with M labels (2 <= M <= 1024,
+ * 1 <= W, H, W*H*M < 2^31).  cuda_stream: a cudaStream_t to order all work on,
+ * or NULL for a stream the handle creates (blocking with respect to the legacy
+ * default stream).  Allocates the message buffers.  On error *out is NULL. */
+bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_handle *out);
+
+/* Unary potential g_i(x) (Eq. 1): dev_unary [H][W][M], float32 g > 0 for
+ * BP_F32, int32 energies E_u >= 0 for BP_I32.  Copied into the handle. */
+bp_status bp_set_unary(bp_handle h, const void *dev_unary);
+
+/* Pairwise potential with the sparse compatibility property (Sec. 4):
+ * host_table[d + T] = f(d), d = x_i - x_j (sender minus receiver label),
+ * -T <= d <= T; every pair with |d| > T has the value fbar.
+ * BP_F32: float32 table, f > 0, fbar >= 0 (fbar = 0 is the pruned form Eq. 8).
+ * BP_I32: int32 energies E(d) >= 0 and Ebar = fbar (an integer); since the
+ * max-product form Eq. 11 is exact only when f >= fbar (Sec. 5), i.e.
+ * E(d) <= Ebar, a table with some E(d) > Ebar returns BP_ERR_POTENTIAL.
+ * 0 <= T; T >= M - 1 makes the band cover every label pair. */
+bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fbar);
+
+/* Uniform initial messages: 1/M (sum), 0 (min-sum), log(1/M) (log mode). */
+bp_status bp_reset_messages(bp_handle h);
+
+/* Run n_iters iterations of the O(mM) update under `schedule`.
+ * mode: BP_SUM (needs BP_F32), BP_MAX (needs BP_I32), or BP_SUM|BP_LOG and
+ * BP_SUM|BP_LOG|BP_RECORD (log-messages, BP_SYNC only).  Messages are
+ * normalised after each update (sum 1, or minimum 0 for min-sum). */
+bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule);
+
+/* Run n_iters synchronous iterations of the dense O(M^2) update (Eq. 2 or
+ * Eq. 9), the baseline the O(mM) update is measured against. */
+bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind);
+
+/* Beliefs (Eq. 3) into dev_out [H][W][M]: float32 normalised beliefs
+ * (BP_F32; in log mode the normalised log-beliefs) or int32 min-sum beliefs
+ * E_u + sum of incoming messages (BP_I32).  dev_map (nullable) [H][W] int32
+ * receives the MAP label: argmax (sum) / argmin (min-sum), lowest label on ties. */
+bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map);
+
+/* Copy the current message planes out / in ([4][H][W][M], dtype of the
+ * handle; log-messages in log mode).  Used to checkpoint or inject a state. */
+bp_status bp_get_messages(bp_handle h, void *dev_planes);
+bp_status bp_set_messages(bp_handle h, const void *dev_planes);
+
+/* Reverse mode of the recorded log-domain sum-product run (bp_iterate with
+ * BP_SUM|BP_LOG|BP_RECORD) followed by bp_beliefs.  Given
+ * dev_dlogb = dL/d log b [H][W][M], writes dev_dlogg = dL/d log g [H][W][M]
+ * and, in float64, host_dtable[d + T] = dL/d f(d) (2T + 1 values) and
+ * *host_dfbar = dL/d fbar, with f(d) and fbar independent parameters.
+ * Synchronises the handle's stream. */
+bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
+                      double *host_dfbar);
+
+/* Checkpoint interval used by BP_RECORD runs (default 5). */
+bp_status bp_set_checkpoint_interval(bp_handle h, int every);
+
+/* Wait for the handle's stream; reports device errors and time-outs. */
+bp_status bp_sync(bp_handle h);
+
+/* Last error message of the handle (never NULL; "" if none).  Valid until
+ * the next call on the handle.  bp_last_error(NULL) reports errors of
+ * bp_create and of calls given a NULL handle. */
+const char *bp_last_error(bp_handle h);
+
+/* Release everything the handle owns.  NULL is ignored. */
+void bp_destroy(bp_handle h);
+
+/* ---- tuning ---------------------------------------------------------------
+ * The O(mM) kernel assigns L lanes to a node, each lane holding V = 4C
+ * consecutive labels (L * 4C = padded label count).  bp_set_layout picks
+ * (L, C); bp_autotune times every layout available for the handle's
+ * (M, T, mode) and keeps the fastest. */
+bp_status bp_set_layout(bp_handle h, int lanes_per_node, int vec_chunks);
+bp_status bp_get_layout(bp_handle h, int *lanes_per_node, int *vec_chunks);
+bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms);
+
+/* Number of kernel launches the library issued on this handle so far. */
+long long bp_launch_count(bp_handle h);
+
+/* Library version, (major << 16) | minor. */
+int bp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BPGRID_BP_H */

@@ -1,0 +1,258 @@
+"""Python binding of the bpgrid C ABI (include/bp.h): argument marshalling only.
+
+Every function below has the name of the C entry point it calls and passes
+torch tensors as raw device pointers.  All arithmetic runs in the CUDA
+library; there is no CPU path.  If the library has not been built the import
+of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbpgrid.so")
+
+BP_OK, BP_ERR_ARG, BP_ERR_STATE, BP_ERR_CUDA, BP_ERR_OOM, BP_ERR_POTENTIAL, BP_ERR_TIMEOUT, \
+    BP_ERR_UNSUPPORTED = range(8)
+BP_SUM, BP_MAX, BP_LOG, BP_RECORD = 0, 1, 2, 4
+BP_SYNC, BP_REDBLACK = 0, 1
+BP_F32, BP_I32 = 0, 1
+BP_DENSE_CUDA_CORE, BP_DENSE_BF16_TC = 0, 1
+STATUS_NAMES = {0: "BP_OK", 1: "BP_ERR_ARG", 2: "BP_ERR_STATE", 3: "BP_ERR_CUDA", 4: "BP_ERR_OOM",
+                5: "BP_ERR_POTENTIAL", 6: "BP_ERR_TIMEOUT", 7: "BP_ERR_UNSUPPORTED"}
+SCHEDULES = {"sync": BP_SYNC, "redblack": BP_REDBLACK}
+
+
+class BPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run paper_1010_0012_gb300.build.build())")
+    lib = ctypes.CDLL(LIB_PATH)
+    I, P, D = ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+    sig = {
+        "bp_create": ([I, I, I, I, P, ctypes.POINTER(P)], I),
+        "bp_set_unary": ([P, P], I),
+        "bp_set_potential": ([P, P, I, D], I),
+        "bp_reset_messages": ([P], I),
+        "bp_iterate": ([P, I, I, I], I),
+        "bp_iterate_dense": ([P, I, I], I),
+        "bp_beliefs": ([P, P, P], I),
+        "bp_get_messages": ([P, P], I),
+        "bp_set_messages": ([P, P], I),
+        "bp_backward": ([P, P, P, P, P], I),
+        "bp_set_checkpoint_interval": ([P, I], I),
+        "bp_sync": ([P], I),
+        "bp_last_error": ([P], ctypes.c_char_p),
+        "bp_destroy": ([P], None),
+        "bp_set_layout": ([P, I, I], I),
+        "bp_get_layout": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bp_autotune": ([P, I, I, ctypes.POINTER(ctypes.c_float)], I),
+        "bp_launch_count": ([P], ctypes.c_longlong),
+        "bp_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def _check(h, st):
+    if st != BP_OK:
+        raise BPError(st, _lib.bp_last_error(h).decode())
+
+
+def _dptr(t: torch.Tensor, dtype, numel=None):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ---- one function per C entry point -------------------------------------------
+
+def bp_version():
+    return _lib.bp_version()
+
+
+def bp_create(W, H, M, dtype=BP_F32, stream=None):
+    h = ctypes.c_void_p()
+    st = _lib.bp_create(W, H, M, dtype, _stream_ptr(stream), ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def bp_destroy(h):
+    _lib.bp_destroy(h)
+
+
+def bp_set_unary(h, unary: torch.Tensor, dtype):
+    _check(h, _lib.bp_set_unary(h, _dptr(unary, torch.float32 if dtype == BP_F32 else torch.int32)))
+
+
+def bp_set_potential(h, table, T: int, fbar: float, dtype):
+    import numpy as np
+    arr = np.ascontiguousarray(table, dtype=np.float32 if dtype == BP_F32 else np.int32)
+    if arr.size != 2 * T + 1:
+        raise ValueError("table must hold 2T + 1 values")
+    _check(h, _lib.bp_set_potential(h, arr.ctypes.data_as(ctypes.c_void_p), int(T), float(fbar)))
+
+
+def bp_reset_messages(h):
+    _check(h, _lib.bp_reset_messages(h))
+
+
+def bp_iterate(h, n_iters, mode=BP_SUM, schedule=BP_SYNC):
+    _check(h, _lib.bp_iterate(h, int(n_iters), int(mode), int(schedule)))
+
+
+def bp_iterate_dense(h, n_iters, kind=BP_DENSE_CUDA_CORE):
+    _check(h, _lib.bp_iterate_dense(h, int(n_iters), int(kind)))
+
+
+def bp_beliefs(h, out: torch.Tensor, map_out: Optional[torch.Tensor] = None):
+    mp = None if map_out is None else _dptr(map_out, torch.int32)
+    _check(h, _lib.bp_beliefs(h, ctypes.c_void_p(out.data_ptr()), mp))
+
+
+def bp_get_messages(h, planes: torch.Tensor):
+    _check(h, _lib.bp_get_messages(h, ctypes.c_void_p(planes.data_ptr())))
+
+
+def bp_set_messages(h, planes: torch.Tensor):
+    if not planes.is_contiguous() or not planes.is_cuda:
+        raise ValueError("expected a contiguous CUDA tensor")
+    _check(h, _lib.bp_set_messages(h, ctypes.c_void_p(planes.data_ptr())))
+
+
+def bp_backward(h, dlogb: torch.Tensor, dlogg: torch.Tensor, n_table: int):
+    import numpy as np
+    dtab = np.zeros(n_table, dtype=np.float64)
+    dfbar = ctypes.c_double(0.0)
+    _check(h, _lib.bp_backward(h, _dptr(dlogb, torch.float32), _dptr(dlogg, torch.float32),
+                               dtab.ctypes.data_as(ctypes.c_void_p), ctypes.byref(dfbar)))
+    return dtab, dfbar.value
+
+
+def bp_set_checkpoint_interval(h, every):
+    _check(h, _lib.bp_set_checkpoint_interval(h, int(every)))
+
+
+def bp_sync(h):
+    _check(h, _lib.bp_sync(h))
+
+
+def bp_last_error(h=None):
+    return _lib.bp_last_error(h).decode()
+
+
+def bp_set_layout(h, L, C):
+    _check(h, _lib.bp_set_layout(h, int(L), int(C)))
+
+
+def bp_get_layout(h):
+    L, C = ctypes.c_int(), ctypes.c_int()
+    _check(h, _lib.bp_get_layout(h, ctypes.byref(L), ctypes.byref(C)))
+    return L.value, C.value
+
+
+def bp_autotune(h, mode, n_iters=3):
+    ms = ctypes.c_float(0.0)
+    _check(h, _lib.bp_autotune(h, int(mode), int(n_iters), ctypes.byref(ms)))
+    return ms.value
+
+
+def bp_launch_count(h):
+    return _lib.bp_launch_count(h)
+
+
+# ---- a thin owner of one handle -------------------------------------------------
+
+class BPGrid:
+    """One H x W grid with M labels; wraps a bp_handle (no arithmetic here)."""
+
+    def __init__(self, W, H, M, dtype=BP_F32, stream=None):
+        self.W, self.H, self.M, self.dtype = W, H, M, dtype
+        self.T = None
+        self.h = bp_create(W, H, M, dtype, stream)
+
+    def close(self):
+        if self.h is not None:
+            bp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def tdtype(self):
+        return torch.float32 if self.dtype == BP_F32 else torch.int32
+
+    def set_unary(self, unary: torch.Tensor):
+        if tuple(unary.shape) != (self.H, self.W, self.M):
+            raise ValueError("unary must be [H][W][M]")
+        bp_set_unary(self.h, unary, self.dtype)
+
+    def set_potential(self, table, T, fbar):
+        bp_set_potential(self.h, table, T, fbar, self.dtype)
+        self.T = T
+
+    def reset(self):
+        bp_reset_messages(self.h)
+
+    def iterate(self, n, mode=None, schedule="sync"):
+        if mode is None:
+            mode = BP_SUM if self.dtype == BP_F32 else BP_MAX
+        bp_iterate(self.h, n, mode, SCHEDULES.get(schedule, schedule))
+
+    def iterate_dense(self, n, kind=BP_DENSE_CUDA_CORE):
+        bp_iterate_dense(self.h, n, kind)
+
+    def beliefs(self, with_map=True):
+        out = torch.empty((self.H, self.W, self.M), dtype=self.tdtype, device="cuda")
+        mp = torch.empty((self.H, self.W), dtype=torch.int32, device="cuda") if with_map else None
+        bp_beliefs(self.h, out, mp)
+        return (out, mp) if with_map else out
+
+    def get_messages(self):
+        out = torch.empty((4, self.H, self.W, self.M), dtype=self.tdtype, device="cuda")
+        bp_get_messages(self.h, out)
+        return out
+
+    def set_messages(self, planes: torch.Tensor):
+        if tuple(planes.shape) != (4, self.H, self.W, self.M) or planes.dtype != self.tdtype:
+            raise ValueError("planes must be [4][H][W][M] of the handle's dtype")
+        bp_set_messages(self.h, planes)
+
+    def sync(self):
+        bp_sync(self.h)
+
+    @property
+    def launches(self):
+        return bp_launch_count(self.h)

@@ -1,0 +1,323 @@
+// O(mM) message update kernels, register/shuffle form (band half-width T <= 8).
+//
+// One group of L lanes handles one node; lane q of the group holds the V = 4C
+// consecutive labels [qV, qV + V) of every vector of that node.  Per node the
+// group reads the unary and the four incoming messages once (5 x Mp words),
+// forms the four products h of Eq. 5 in registers, and writes the four outgoing
+// messages (4 x Mp words) straight into the neighbours' incoming planes:
+//
+//   sum-product (Eq. 7):
+//     S      = sum_x h(x)                        (group shuffle reduction)
+//     B(x_j) = sum_{|d| <= T} [f(d) - fbar] h(x_j + d)   (band; halo via shuffles)
+//     u(x_j) = B(x_j) + fbar S,  m(x_j) = u(x_j) / sum_x u(x)
+//   min-sum (Eq. 11 in energies):
+//     Hmin   = min_x h(x)
+//     u(x_j) = min( min_{|d| <= T} [E(d) + h(x_j + d)], Ebar + Hmin ),  m = u - min_x u
+//
+// The band is clipped to the labels [0, M) (a label outside has no h).  The
+// normaliser sum_x u(x) of Eq. 7 is obtained without a second pass over u:
+//   sum_{x_j} B(x_j) = sum_{x_i} h(x_i) c(x_i),  c(x_i) = sum of f(d) - fbar over
+//   the d that keep x_j = x_i - d inside [0, M),
+// so sum_x u = sum_x h(x) (c(x) + M fbar), reduced together with S.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bp_internal.h"
+
+namespace bpg {
+
+#define BPG_FULL 0xffffffffu
+constexpr int32_t kIntBig = 1 << 30;   // "no label" energy, far above any message
+constexpr float kLogNone = -1.0e30f;   // "no label" log-value
+
+// ---------------------------------------------------------------- vectors ----
+template <int V>
+__device__ __forceinline__ void ld_vec(float (&v)[V], const float *p) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + i);
+        v[4 * i + 0] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+}
+template <int V>
+__device__ __forceinline__ void ld_vec(int32_t (&v)[V], const int32_t *p) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i) {
+        const int4 t = __ldg(reinterpret_cast<const int4 *>(p) + i);
+        v[4 * i + 0] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+    }
+}
+template <int V>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[V]) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i)
+        reinterpret_cast<float4 *>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+template <int V>
+__device__ __forceinline__ void st_vec(int32_t *p, const int32_t (&v)[V]) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i)
+        reinterpret_cast<int4 *>(p)[i] = make_int4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+template <int V, typename T>
+__device__ __forceinline__ void fill_vec(T (&v)[V], T x) {
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[i] = x;
+}
+
+// ------------------------------------------------------- group reductions ----
+template <int L>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(BPG_FULL, v, o);
+    return v;
+}
+template <int L>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(BPG_FULL, v, o));
+    return v;
+}
+template <int L>
+__device__ __forceinline__ int32_t group_min(int32_t v) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(BPG_FULL, v, o));
+    return v;
+}
+
+// Band window: win[T + j] = h(qV + j) for j in [-T, V + T), taken from the
+// neighbouring lanes of the group; labels outside [0, L*V) get `none`.
+template <int L, int V, int T, typename E>
+__device__ __forceinline__ void band_window(E (&win)[V + 2 * T], const E (&h)[V], int q, E none) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) win[T + k] = h[k];
+#pragma unroll
+    for (int j = 1; j <= T; ++j) {               // label offset -j
+        const int delta = (j + V - 1) / V;       // source lane q - delta
+        const int idx = delta * V - j;           // its register
+        E v = none;
+        if (L > 1) {
+            v = __shfl_up_sync(BPG_FULL, h[idx], delta, L);
+            if (q < delta) v = none;
+        }
+        win[T - j] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {                // label offset V + j
+        const int delta = (V + j) / V;           // source lane q + delta
+        const int idx = V + j - delta * V;
+        E v = none;
+        if (L > 1) {
+            v = __shfl_down_sync(BPG_FULL, h[idx], delta, L);
+            if (q + delta >= L) v = none;
+        }
+        win[T + V + j] = v;
+    }
+}
+
+// Node of slot `slot` for a synchronous sweep (parity < 0) or a red-black
+// half-step (nodes with (r + c) % 2 == parity).  Returns false past the end.
+__device__ __forceinline__ bool slot_node(int slot, int nslots, int W, int parity, int &r, int &c) {
+    r = 0;
+    c = 0;
+    if (slot >= nslots) return false;
+    if (parity < 0) {
+        r = slot / W;
+        c = slot - r * W;
+        return true;
+    }
+    const int Wh = (W + 1) >> 1;
+    r = slot / Wh;
+    c = 2 * (slot - r * Wh) + ((r + parity) & 1);
+    if (c >= W) { c = 0; return false; }
+    return true;
+}
+
+__device__ __forceinline__ int num_slots(int W, int H, int parity) {
+    return parity < 0 ? W * H : ((W + 1) >> 1) * H;
+}
+
+// Outgoing direction t: 0 to the left neighbour (stored in its plane 1),
+// 1 to the right (plane 0), 2 up (plane 3), 3 down (plane 2).  Eq. 5 leaves
+// out the message that came from that neighbour, i.e. incoming plane t.
+__device__ __forceinline__ long long out_offset(int t, int r, int c, int W, long long plane, int Mp) {
+    const int dst_plane = t ^ 1;
+    const int dr = (t == 2) ? -1 : (t == 3) ? 1 : 0;
+    const int dc = (t == 0) ? -1 : (t == 1) ? 1 : 0;
+    return dst_plane * plane + ((long long)(r + dr) * W + (c + dc)) * Mp;
+}
+
+// ----------------------------------------------- sum-product (linear/log) ----
+// LOG = false: linear messages, g is the unary.  LOG = true: log-messages,
+// g holds log g; h is formed as exp(log h - max log h), which leaves the
+// normalised result unchanged.
+template <int L, int C, int T, bool LOG>
+__global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
+    constexpr int V = 4 * C;
+    constexpr int GPB = kBlock / L;
+    const int q = threadIdx.x & (L - 1);
+    const int grp = threadIdx.x / L;
+    const int W = a.d.W, H = a.d.H, M = a.d.M, Mp = a.d.Mp;
+    const long long plane = a.d.plane;
+
+    float w[2 * T + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * T + 1; ++i) w[i] = a.w[i];
+    const float fbar = a.fbar;
+
+    // per-label normaliser weights c(x) + M fbar (0 on padded labels)
+    float cz[V];
+    bool lab_ok[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int x = q * V + k;
+        float cx = 0.f;
+#pragma unroll
+        for (int d = -T; d <= T; ++d)
+            if (x - d >= 0 && x - d < M) cx += w[d + T];
+        lab_ok[k] = x < M;
+        cz[k] = lab_ok[k] ? cx + (float)M * fbar : 0.f;
+    }
+
+    const int nslots = num_slots(W, H, a.parity);
+    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
+        int r, c;
+        const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
+        const long long off = ((long long)r * W + c) * Mp + q * V;
+        const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
+        const float absent = LOG ? 0.f : 1.f;
+
+        float gv[V], m[4][V];
+        if (valid) ld_vec<V>(gv, a.g + off); else fill_vec<V>(gv, LOG ? 0.f : 0.f);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (has[s]) ld_vec<V>(m[s], a.in + s * plane + off);
+            else fill_vec<V>(m[s], absent);
+        }
+
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float h[V];
+            if (!LOG) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    // product of the unary and the three messages other than m[t]
+                    const float p01 = (t == 0) ? m[1][k] : (t == 1) ? m[0][k] : m[0][k] * m[1][k];
+                    const float p23 = (t == 2) ? m[3][k] : (t == 3) ? m[2][k] : m[2][k] * m[3][k];
+                    h[k] = gv[k] * p01 * p23;
+                }
+            } else {
+                float amax = kLogNone;
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    float s = gv[k];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (u != t) s += m[u][k];
+                    h[k] = lab_ok[k] ? s : kLogNone;
+                    amax = fmaxf(amax, h[k]);
+                }
+                amax = group_max<L>(amax);
+#pragma unroll
+                for (int k = 0; k < V; ++k) h[k] = lab_ok[k] ? expf(h[k] - amax) : 0.f;
+            }
+
+            float S = 0.f, Z = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                S += h[k];
+                Z = fmaf(h[k], cz[k], Z);
+            }
+            S = group_sum<L>(S);
+            Z = group_sum<L>(Z);
+
+            float win[V + 2 * T];
+            band_window<L, V, T, float>(win, h, q, 0.f);
+            const float inv = 1.f / Z;
+            const float base_term = fbar * S * inv;
+            float o[V];
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int d = -T; d <= T; ++d) acc = fmaf(w[d + T], win[T + k + d], acc);
+                const float mv = fmaf(acc, inv, base_term);
+                o[k] = lab_ok[k] ? (LOG ? logf(mv) : mv) : 0.f;
+            }
+            if (has[t]) st_vec<V>(a.out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
+        }
+    }
+}
+
+// ------------------------------------------------------------- min-sum ------
+template <int L, int C, int T>
+__global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
+    constexpr int V = 4 * C;
+    constexpr int GPB = kBlock / L;
+    const int q = threadIdx.x & (L - 1);
+    const int grp = threadIdx.x / L;
+    const int W = a.d.W, H = a.d.H, M = a.d.M, Mp = a.d.Mp;
+    const long long plane = a.d.plane;
+
+    int32_t w[2 * T + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * T + 1; ++i) w[i] = a.w[i];
+    const int32_t ebar = a.ebar;
+    bool lab_ok[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) lab_ok[k] = q * V + k < M;
+
+    const int nslots = num_slots(W, H, a.parity);
+    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
+        int r, c;
+        const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
+        const long long off = ((long long)r * W + c) * Mp + q * V;
+        const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
+
+        int32_t ev[V], m[4][V];
+        if (valid) ld_vec<V>(ev, a.e + off); else fill_vec<V, int32_t>(ev, 0);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (has[s]) ld_vec<V>(m[s], a.in + s * plane + off);
+            else fill_vec<V, int32_t>(m[s], 0);
+        }
+
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int32_t h[V];
+            int32_t hmin = kIntBig;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                int32_t s = ev[k];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u != t) s += m[u][k];
+                h[k] = lab_ok[k] ? s : kIntBig;
+                hmin = min(hmin, h[k]);
+            }
+            hmin = group_min<L>(hmin);
+
+            int32_t win[V + 2 * T];
+            band_window<L, V, T, int32_t>(win, h, q, kIntBig);
+            const int32_t flat = ebar + hmin;
+            int32_t u[V];
+            int32_t umin = kIntBig;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                int32_t b = flat;
+#pragma unroll
+                for (int d = -T; d <= T; ++d) b = min(b, w[d + T] + win[T + k + d]);
+                u[k] = lab_ok[k] ? b : kIntBig;
+                umin = min(umin, u[k]);
+            }
+            umin = group_min<L>(umin);
+#pragma unroll
+            for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
+            if (has[t]) st_vec<V>(a.out + out_offset(t, r, c, W, plane, Mp) + q * V, u);
+        }
+    }
+}
+
+}  // namespace bpg

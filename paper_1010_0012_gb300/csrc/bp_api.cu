@@ -1,0 +1,579 @@
+// C-ABI layer: handle ownership, argument validation, the iteration driver
+// (schedules, CUDA-graph replay) and the tuning entry points.  Declarations
+// and the contract of every call are in include/bp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bp.h"
+#include "bp_internal.h"
+#include "bp_ctx.h"
+
+using namespace bpg;
+
+namespace {
+
+thread_local std::string g_global_err;
+
+bp_status fail(bp_ctx *h, bp_status st, const std::string &msg) {
+    if (h) h->err = msg; else g_global_err = msg;
+    return st;
+}
+
+bp_status cuda_fail(bp_ctx *h, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(h, BP_ERR_OOM, m);
+    return fail(h, BP_ERR_CUDA, m);
+}
+
+#define BP_CK(h, call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+    } while (0)
+
+size_t elem_bytes() { return 4; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ helpers --
+
+bp_status bpg_check_device(bp_ctx *h) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+    if (dev != h->device) return fail(h, BP_ERR_STATE, "the current CUDA device differs from the handle's device");
+    return BP_OK;
+}
+
+static void clear_graphs(bp_ctx *h) {
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+}
+
+static bp_status ensure_buffer(bp_ctx *h, void **p, size_t bytes, const char *what) {
+    if (*p) return BP_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return cuda_fail(h, e, what);
+    }
+    return BP_OK;
+}
+
+size_t bpg_plane_bytes(const bp_ctx *h) { return (size_t)h->dims.plane * elem_bytes(); }
+size_t bpg_state_bytes(const bp_ctx *h) { return 4 * bpg_plane_bytes(h); }
+
+// Make the current message buffer hold the representation `want_log`.
+static bp_status materialize(bp_ctx *h, bool want_log) {
+    const long long rows = 4LL * h->W * h->H;
+    if (h->msg_uniform) {
+        if (h->dtype == BP_I32) {
+            BP_CK(h, launch_fill_messages_i32((int32_t *)h->msg[h->cur], rows, h->M, h->Mp, 0, h->stream));
+        } else {
+            const float v = want_log ? -logf((float)h->M) : 1.0f / (float)h->M;
+            BP_CK(h, launch_fill_messages_f32((float *)h->msg[h->cur], rows, h->M, h->Mp, v, h->stream));
+        }
+        h->launches += 1;
+        h->msg_uniform = false;
+        h->msg_log = want_log && h->dtype == BP_F32;
+        return BP_OK;
+    }
+    if (h->dtype == BP_F32 && h->msg_log != want_log) {
+        BP_CK(h, launch_domain_convert((float *)h->msg[h->cur], rows, h->M, h->Mp, want_log ? 1 : 0, h->stream));
+        h->launches += 1;
+        h->msg_log = want_log;
+    }
+    return BP_OK;
+}
+
+static bp_status ensure_log_unary(bp_ctx *h) {
+    if (h->log_unary_valid) return BP_OK;
+    bp_status st = ensure_buffer(h, (void **)&h->log_unary, (size_t)h->W * h->H * h->Mp * 4, "log unary");
+    if (st) return st;
+    BP_CK(h, launch_domain_convert_copy((const float *)h->unary, h->log_unary, (long long)h->W * h->H, h->M, h->Mp,
+                                        h->stream));
+    h->launches += 1;
+    h->log_unary_valid = true;
+    return BP_OK;
+}
+
+// Issue the kernels of one O(mM) iteration (one or two launches).
+static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int &count) {
+    const bool is_log = (mode & BP_LOG) != 0;
+    const int nsteps = sched == BP_REDBLACK ? 2 : 1;
+    for (int step = 0; step < nsteps; ++step) {
+        const int parity = sched == BP_REDBLACK ? step : -1;
+        void *in = h->msg[cur];
+        void *out = sched == BP_REDBLACK ? h->msg[cur] : h->msg[cur ^ 1];
+        cudaError_t e;
+        if (h->dtype == BP_I32) {
+            if (h->fast) {
+                BandArgsI a{};
+                a.e = (const int32_t *)h->unary; a.in = (const int32_t *)in; a.out = (int32_t *)out;
+                a.d = h->dims; a.parity = parity; a.T = h->Teff;
+                for (int i = 0; i < 2 * h->Teff + 1; ++i) a.w[i] = h->wi[i];
+                a.ebar = h->ebar;
+                e = launch_band_min(a, h->layout, h->blocks_override, h->stream);
+            } else {
+                BandArgsGenericI a{(const int32_t *)h->unary, (const int32_t *)in, (int32_t *)out, h->dims,
+                                   parity, h->Teff, h->d_wi, h->ebar};
+                e = launch_band_min_generic(a, h->stream);
+            }
+        } else if (h->fast) {
+            BandArgsF a{};
+            a.g = is_log ? h->log_unary : (const float *)h->unary;
+            a.in = (const float *)in; a.out = (float *)out;
+            a.d = h->dims; a.parity = parity; a.T = h->Teff;
+            for (int i = 0; i < 2 * h->Teff + 1; ++i) a.w[i] = h->wf[i];
+            a.fbar = h->fbarf;
+            e = is_log ? launch_band_log(a, h->layout, h->blocks_override, h->stream)
+                       : launch_band_sum(a, h->layout, h->blocks_override, h->stream);
+        } else {
+            if (is_log) return cudaErrorNotSupported;
+            BandArgsGenericF a{(const float *)h->unary, (const float *)in, (float *)out, h->dims, parity,
+                               h->Teff, h->d_wf, h->fbarf};
+            e = launch_band_sum_generic(a, h->stream);
+        }
+        if (e != cudaSuccess) return e;
+        ++count;
+    }
+    if (sched != BP_REDBLACK) cur ^= 1;
+    return cudaSuccess;
+}
+
+// Run n iterations, through a cached CUDA graph when possible.  `per_iter`
+// (nullable) is called after every iteration with the iteration index (used
+// by recording); recording runs are issued directly.
+static bp_status run_iterations(bp_ctx *h, int n, int mode, int sched) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BP_CK(h, cudaStreamIsCapturing(h->stream, &cap));
+    const bool use_graph = h->use_graphs && cap == cudaStreamCaptureStatusNone && n > 1;
+    if (!use_graph) {
+        for (int it = 0; it < n; ++it) {
+            int count = 0;
+            cudaError_t e = issue_iteration(h, mode, sched, h->cur, count);
+            if (e != cudaSuccess) return cuda_fail(h, e, "O(mM) update launch");
+            h->launches += count;
+        }
+        return BP_OK;
+    }
+    const GraphKey key{n, mode, sched, h->cur, h->layout.L, h->layout.C, h->blocks_override};
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        BP_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        int cur = h->cur, count = 0;
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < n && e == cudaSuccess; ++k) e = issue_iteration(h, mode, sched, cur, count);
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "O(mM) update capture"); }
+        if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        it = h->graphs.emplace(key, GraphEntry{ex, count, cur}).first;
+    }
+    BP_CK(h, cudaGraphLaunch(it->second.exec, h->stream));
+    h->launches += it->second.launches;
+    h->cur = it->second.end_cur;
+    return BP_OK;
+}
+
+// ------------------------------------------------------------------- ABI ----
+
+extern "C" {
+
+int bp_version(void) { return (0 << 16) | 3; }
+
+const char *bp_last_error(bp_handle h) { return h ? h->err.c_str() : g_global_err.c_str(); }
+
+long long bp_launch_count(bp_handle h) { return h ? h->launches : -1; }
+
+bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_handle *out) {
+    g_global_err.clear();
+    if (!out) return fail(nullptr, BP_ERR_ARG, "bp_create: out is NULL");
+    *out = nullptr;
+    if (W < 1 || H < 1) return fail(nullptr, BP_ERR_ARG, "bp_create: W and H must be >= 1");
+    if (M < 2 || M > 1024) return fail(nullptr, BP_ERR_ARG, "bp_create: M must be in [2, 1024]");
+    if (dtype != BP_F32 && dtype != BP_I32) return fail(nullptr, BP_ERR_ARG, "bp_create: unknown dtype");
+    const int Mp = padded_labels(M);
+    if ((long long)W * H > (1LL << 30) || (long long)W * H * Mp >= (1LL << 31))
+        return fail(nullptr, BP_ERR_ARG, "bp_create: grid too large (W*H*Mp must be < 2^31)");
+    bp_ctx *h = new bp_ctx();
+    h->W = W; h->H = H; h->M = M; h->Mp = Mp; h->dtype = dtype;
+    h->dims = GridDims{W, H, M, Mp, (long long)W * H * Mp};
+    Layout lays[8];
+    h->layout = layouts_for(Mp, lays, 8) > 0 ? lays[0] : Layout{32, 1};
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { bp_status st = cuda_fail(nullptr, e, "cudaGetDevice"); delete h; return st; }
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+        h->own_stream = false;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamDefault);
+        if (e != cudaSuccess) { bp_status st = cuda_fail(nullptr, e, "cudaStreamCreate"); delete h; return st; }
+        h->own_stream = true;
+    }
+    const size_t ub = (size_t)W * H * Mp * 4;
+    bp_status st = BP_OK;
+    if (!st) st = ensure_buffer(h, &h->unary, ub, "unary buffer");
+    if (!st) st = ensure_buffer(h, &h->msg[0], bpg_state_bytes(h), "message buffer 0");
+    if (!st) st = ensure_buffer(h, &h->msg[1], bpg_state_bytes(h), "message buffer 1");
+    if (!st) st = ensure_buffer(h, (void **)&h->d_status, sizeof(int), "status word");
+    if (!st) {
+        e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "cudaMemsetAsync");
+    }
+    if (st) {
+        g_global_err = h->err;
+        bp_destroy(h);
+        return st;
+    }
+    *out = h;
+    return BP_OK;
+}
+
+void bp_destroy(bp_handle h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    clear_graphs(h);
+    bpg_free_extras(h);
+    void *bufs[] = {h->unary, h->log_unary, h->msg[0], h->msg[1], h->d_wf, h->d_wi, h->d_dense, h->d_status,
+                    h->tune_buf};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+bp_status bp_set_unary(bp_handle h, const void *dev_unary) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary: NULL handle");
+    h->err.clear();
+    if (!dev_unary) return fail(h, BP_ERR_ARG, "bp_set_unary: NULL unary");
+    if (bp_status st = bpg_check_device(h)) return st;
+    const long long nodes = (long long)h->W * h->H;
+    if (h->dtype == BP_F32)
+        BP_CK(h, launch_pad_copy_f32((const float *)dev_unary, (float *)h->unary, nodes, h->M, h->Mp, 0, h->stream));
+    else
+        BP_CK(h, launch_pad_copy_i32((const int32_t *)dev_unary, (int32_t *)h->unary, nodes, h->M, h->Mp, h->stream));
+    h->launches += 1;
+    h->have_unary = true;
+    h->log_unary_valid = false;
+    h->recorded = false;
+    return BP_OK;
+}
+
+bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fbar) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_potential: NULL handle");
+    h->err.clear();
+    if (!host_table) return fail(h, BP_ERR_ARG, "bp_set_potential: NULL table");
+    if (T < 0 || T > (1 << 20)) return fail(h, BP_ERR_ARG, "bp_set_potential: T out of range");
+    if (!std::isfinite(fbar) || fbar < 0) return fail(h, BP_ERR_ARG, "bp_set_potential: fbar must be finite and >= 0");
+    const int m = 2 * T + 1;
+    const int Teff = std::min(T, h->M - 1);
+    if (h->dtype == BP_F32) {
+        const float *tab = (const float *)host_table;
+        for (int i = 0; i < m; ++i)
+            if (!std::isfinite(tab[i]) || tab[i] < 0)
+                return fail(h, BP_ERR_ARG, "bp_set_potential: table entries must be finite and >= 0");
+        h->tablef.assign(tab, tab + m);
+        h->fbarf = (float)fbar;
+        h->wf.resize(2 * Teff + 1);
+        for (int d = -Teff; d <= Teff; ++d) h->wf[d + Teff] = (float)((double)tab[d + T] - (double)h->fbarf);
+    } else {
+        const int32_t *tab = (const int32_t *)host_table;
+        if (fbar != std::floor(fbar) || fbar >= (double)(1 << 26))
+            return fail(h, BP_ERR_ARG, "bp_set_potential: Ebar must be an integer in [0, 2^26)");
+        const int32_t ebar = (int32_t)fbar;
+        for (int i = 0; i < m; ++i) {
+            if (tab[i] < 0 || tab[i] >= (1 << 26))
+                return fail(h, BP_ERR_ARG, "bp_set_potential: energies must lie in [0, 2^26)");
+            if (tab[i] > ebar)
+                return fail(h, BP_ERR_POTENTIAL,
+                            "bp_set_potential: E(d) > Ebar; Eq. 11 is exact only when f >= fbar (Sec. 5)");
+        }
+        h->tablei.assign(tab, tab + m);
+        h->ebar = ebar;
+        h->wi.resize(2 * Teff + 1);
+        for (int d = -Teff; d <= Teff; ++d) h->wi[d + Teff] = tab[d + T];
+    }
+    h->T = T;
+    h->Teff = Teff;
+    h->fbar = fbar;
+    h->fast = Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, Teff);
+    if (!h->fast) {
+        const size_t wb = (size_t)(2 * Teff + 1) * 4;
+        if (h->d_wf) { cudaFree(h->d_wf); h->d_wf = nullptr; }
+        if (h->d_wi) { cudaFree(h->d_wi); h->d_wi = nullptr; }
+        if (h->dtype == BP_F32) {
+            if (bp_status st = ensure_buffer(h, (void **)&h->d_wf, wb, "band table")) return st;
+            BP_CK(h, cudaMemcpyAsync(h->d_wf, h->wf.data(), wb, cudaMemcpyHostToDevice, h->stream));
+        } else {
+            if (bp_status st = ensure_buffer(h, (void **)&h->d_wi, wb, "band table")) return st;
+            BP_CK(h, cudaMemcpyAsync(h->d_wi, h->wi.data(), wb, cudaMemcpyHostToDevice, h->stream));
+        }
+        // the copy reads pageable host memory owned by the handle's vectors,
+        // which stay alive; make it complete before they can change
+        BP_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
+    h->have_potential = true;
+    h->recorded = false;
+    clear_graphs(h);
+    return BP_OK;
+}
+
+bp_status bp_reset_messages(bp_handle h) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_reset_messages: NULL handle");
+    h->err.clear();
+    h->msg_uniform = true;
+    h->recorded = false;
+    return BP_OK;
+}
+
+bp_status bp_set_layout(bp_handle h, int L, int C) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_layout: NULL handle");
+    h->err.clear();
+    Layout lays[8];
+    const int n = std::min(8, layouts_for(h->Mp, lays, 8));
+    for (int i = 0; i < n; ++i)
+        if (lays[i].L == L && lays[i].C == C) {
+            h->layout = lays[i];
+            if (h->have_potential) h->fast = h->Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, h->Teff);
+            return BP_OK;
+        }
+    return fail(h, BP_ERR_ARG, "bp_set_layout: layout not compiled for this label count");
+}
+
+bp_status bp_get_layout(bp_handle h, int *L, int *C) {
+    if (!h || !L || !C) return fail(h, BP_ERR_ARG, "bp_get_layout: NULL argument");
+    *L = h->layout.L;
+    *C = h->layout.C;
+    return BP_OK;
+}
+
+bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_iterate: NULL handle");
+    h->err.clear();
+    if (n_iters < 0) return fail(h, BP_ERR_ARG, "bp_iterate: n_iters < 0");
+    if (schedule != BP_SYNC && schedule != BP_REDBLACK) return fail(h, BP_ERR_ARG, "bp_iterate: unknown schedule");
+    const int base = mode & 1;
+    const bool is_log = (mode & BP_LOG) != 0, rec = (mode & BP_RECORD) != 0;
+    if (mode & ~(BP_MAX | BP_LOG | BP_RECORD)) return fail(h, BP_ERR_ARG, "bp_iterate: unknown mode bits");
+    if (base == BP_MAX && h->dtype != BP_I32) return fail(h, BP_ERR_ARG, "bp_iterate: BP_MAX needs a BP_I32 handle");
+    if (base == BP_SUM && h->dtype != BP_F32) return fail(h, BP_ERR_ARG, "bp_iterate: BP_SUM needs a BP_F32 handle");
+    if ((is_log || rec) && base != BP_SUM) return fail(h, BP_ERR_ARG, "bp_iterate: BP_LOG/BP_RECORD are sum-product flags");
+    if (rec && !is_log) return fail(h, BP_ERR_ARG, "bp_iterate: BP_RECORD needs BP_LOG");
+    if (rec && schedule != BP_SYNC) return fail(h, BP_ERR_ARG, "bp_iterate: BP_RECORD needs BP_SYNC");
+    if (!h->have_unary || !h->have_potential)
+        return fail(h, BP_ERR_STATE, "bp_iterate: set the unary and the potential first");
+    if (is_log && !h->fast)
+        return fail(h, BP_ERR_UNSUPPORTED, "bp_iterate: log mode needs T <= 8 and M <= 512");
+    if (bp_status st = bpg_check_device(h)) return st;
+    if (is_log) {
+        if (bp_status st = ensure_log_unary(h)) return st;
+    }
+    if (bp_status st = materialize(h, is_log)) return st;
+    if (rec) return bpg_record_forward(h, n_iters);
+    h->recorded = false;
+    if (n_iters == 0) return BP_OK;
+    return run_iterations(h, n_iters, mode & (BP_MAX | BP_LOG), schedule);
+}
+
+bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_iterate_dense: NULL handle");
+    h->err.clear();
+    if (n_iters < 0) return fail(h, BP_ERR_ARG, "bp_iterate_dense: n_iters < 0");
+    if (!h->have_unary || !h->have_potential)
+        return fail(h, BP_ERR_STATE, "bp_iterate_dense: set the unary and the potential first");
+    if (bp_status st = bpg_check_device(h)) return st;
+    if (bp_status st = materialize(h, false)) return st;
+    h->recorded = false;
+    if (kind == BP_DENSE_BF16_TC) {
+        if (h->dtype != BP_F32) return fail(h, BP_ERR_ARG, "bp_iterate_dense: the tensor-core baseline is sum-product");
+        return bpg_dense_tc_iterate(h, n_iters);
+    }
+    if (kind != BP_DENSE_CUDA_CORE) return fail(h, BP_ERR_ARG, "bp_iterate_dense: unknown kind");
+    // the full M x M table, F[x_i][x_j] (f, or E for min-sum)
+    if (!h->d_dense) {
+        const size_t bytes = (size_t)h->M * h->M * 4;
+        std::vector<float> F;
+        std::vector<int32_t> V;
+        if (h->dtype == BP_F32) F.resize((size_t)h->M * h->M); else V.resize((size_t)h->M * h->M);
+        for (int xi = 0; xi < h->M; ++xi)
+            for (int xj = 0; xj < h->M; ++xj) {
+                const int d = xi - xj;
+                const bool in_band = d >= -h->T && d <= h->T;
+                if (h->dtype == BP_F32) F[(size_t)xi * h->M + xj] = in_band ? h->tablef[d + h->T] : h->fbarf;
+                else V[(size_t)xi * h->M + xj] = in_band ? h->tablei[d + h->T] : h->ebar;
+            }
+        if (bp_status st = ensure_buffer(h, &h->d_dense, bytes, "dense table")) return st;
+        BP_CK(h, cudaMemcpyAsync(h->d_dense, h->dtype == BP_F32 ? (const void *)F.data() : (const void *)V.data(),
+                                 bytes, cudaMemcpyHostToDevice, h->stream));
+        BP_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    for (int it = 0; it < n_iters; ++it) {
+        if (h->dtype == BP_F32) {
+            DenseArgsF a{(const float *)h->unary, (const float *)h->msg[h->cur], (float *)h->msg[h->cur ^ 1], h->dims,
+                         (const float *)h->d_dense};
+            BP_CK(h, launch_dense_sum(a, h->stream));
+        } else {
+            DenseArgsI a{(const int32_t *)h->unary, (const int32_t *)h->msg[h->cur], (int32_t *)h->msg[h->cur ^ 1],
+                         h->dims, (const int32_t *)h->d_dense};
+            BP_CK(h, launch_dense_min(a, h->stream));
+        }
+        h->launches += 1;
+        h->cur ^= 1;
+    }
+    return BP_OK;
+}
+
+bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_beliefs: NULL handle");
+    h->err.clear();
+    if (!dev_out) return fail(h, BP_ERR_ARG, "bp_beliefs: NULL output");
+    if (!h->have_unary) return fail(h, BP_ERR_STATE, "bp_beliefs: set the unary first");
+    if (bp_status st = bpg_check_device(h)) return st;
+    if (h->msg_uniform)
+        if (bp_status st = materialize(h, false)) return st;
+    if (h->dtype == BP_F32) {
+        const bool lg = h->msg_log;
+        if (lg)
+            if (bp_status st = ensure_log_unary(h)) return st;
+        BP_CK(h, launch_beliefs_f32(lg ? h->log_unary : (const float *)h->unary, (const float *)h->msg[h->cur], h->dims,
+                                    lg ? 1 : 0, (float *)dev_out, dev_map, h->stream));
+    } else {
+        BP_CK(h, launch_beliefs_i32((const int32_t *)h->unary, (const int32_t *)h->msg[h->cur], h->dims,
+                                    (int32_t *)dev_out, dev_map, h->stream));
+    }
+    h->launches += 1;
+    return BP_OK;
+}
+
+bp_status bp_get_messages(bp_handle h, void *dev_planes) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_get_messages: NULL handle");
+    h->err.clear();
+    if (!dev_planes) return fail(h, BP_ERR_ARG, "bp_get_messages: NULL output");
+    if (bp_status st = bpg_check_device(h)) return st;
+    if (h->msg_uniform)
+        if (bp_status st = materialize(h, false)) return st;
+    const long long rows = 4LL * h->W * h->H;
+    BP_CK(h, launch_unpad_copy(h->msg[h->cur], dev_planes, rows, h->M, h->Mp, h->stream));
+    h->launches += 1;
+    if (h->dtype == BP_F32 && h->msg_log) {
+        BP_CK(h, launch_domain_convert_dense((float *)dev_planes, rows * h->M, 0, h->stream));
+        h->launches += 1;
+    }
+    return BP_OK;
+}
+
+bp_status bp_set_messages(bp_handle h, const void *dev_planes) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_messages: NULL handle");
+    h->err.clear();
+    if (!dev_planes) return fail(h, BP_ERR_ARG, "bp_set_messages: NULL input");
+    if (bp_status st = bpg_check_device(h)) return st;
+    const long long rows = 4LL * h->W * h->H;
+    if (h->dtype == BP_F32)
+        BP_CK(h, launch_pad_copy_f32((const float *)dev_planes, (float *)h->msg[h->cur], rows, h->M, h->Mp, 0, h->stream));
+    else
+        BP_CK(h, launch_pad_copy_i32((const int32_t *)dev_planes, (int32_t *)h->msg[h->cur], rows, h->M, h->Mp,
+                                     h->stream));
+    h->launches += 1;
+    h->msg_uniform = false;
+    h->msg_log = false;
+    h->recorded = false;
+    return BP_OK;
+}
+
+bp_status bp_sync(bp_handle h) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_sync: NULL handle");
+    BP_CK(h, cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    BP_CK(h, cudaMemcpy(&flag, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        BP_CK(h, cudaMemset(h->d_status, 0, sizeof(int)));
+        return fail(h, BP_ERR_TIMEOUT, "a bounded device-side wait gave up (status " + std::to_string(flag) + ")");
+    }
+    return BP_OK;
+}
+
+bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_autotune: NULL handle");
+    h->err.clear();
+    if (n_iters < 1) return fail(h, BP_ERR_ARG, "bp_autotune: n_iters < 1");
+    if (!h->have_unary || !h->have_potential) return fail(h, BP_ERR_STATE, "bp_autotune: set unary and potential first");
+    const bool is_log = (mode & BP_LOG) != 0;
+    if (bp_status st = bpg_check_device(h)) return st;
+    if (is_log)
+        if (bp_status st = ensure_log_unary(h)) return st;
+    if (bp_status st = materialize(h, is_log)) return st;
+    if (bp_status st = ensure_buffer(h, &h->tune_buf, bpg_state_bytes(h), "autotune buffer")) return st;
+    Layout lays[8];
+    const int n = std::min(8, layouts_for(h->Mp, lays, 8));
+    const Layout saved = h->layout;
+    const int saved_cur = h->cur;
+    BP_CK(h, cudaMemcpyAsync(h->tune_buf, h->msg[h->cur], bpg_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    cudaEvent_t e0, e1;
+    BP_CK(h, cudaEventCreate(&e0));
+    BP_CK(h, cudaEventCreate(&e1));
+    float best = 3e38f;
+    Layout best_lay = saved;
+    const int md = mode & (BP_MAX | BP_LOG);
+    for (int i = 0; i < n; ++i) {
+        if (h->Teff > kTMaxFast || !band_fast_available(h->Mp, lays[i], h->Teff)) continue;
+        h->layout = lays[i];
+        h->fast = true;
+        bp_status st = run_iterations(h, n_iters, md, BP_SYNC);        // warm
+        if (!st) st = (cudaEventRecord(e0, h->stream) == cudaSuccess) ? BP_OK : BP_ERR_CUDA;
+        if (!st) st = run_iterations(h, n_iters, md, BP_SYNC);
+        if (!st) st = (cudaEventRecord(e1, h->stream) == cudaSuccess) ? BP_OK : BP_ERR_CUDA;
+        if (!st) st = (cudaEventSynchronize(e1) == cudaSuccess) ? BP_OK : BP_ERR_CUDA;
+        float ms = 0.f;
+        if (!st) cudaEventElapsedTime(&ms, e0, e1);
+        if (st) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            h->layout = saved;
+            return st == BP_ERR_CUDA ? fail(h, st, "bp_autotune: timing failed") : st;
+        }
+        if (ms < best) { best = ms; best_lay = lays[i]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->layout = best_lay;
+    h->fast = h->Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, h->Teff);
+    h->cur = saved_cur;
+    BP_CK(h, cudaMemcpyAsync(h->msg[h->cur], h->tune_buf, bpg_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    if (host_best_ms) *host_best_ms = best / (float)n_iters;
+    return BP_OK;
+}
+
+bp_status bp_set_checkpoint_interval(bp_handle h, int every) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_checkpoint_interval: NULL handle");
+    if (every < 1) return fail(h, BP_ERR_ARG, "bp_set_checkpoint_interval: interval must be >= 1");
+    h->ckpt_every = every;
+    h->recorded = false;
+    return BP_OK;
+}
+
+}  // extern "C"
+
+// Shared with bp_backward.cu / dense_tc.cu.
+bp_status bpg_fail(bp_ctx *h, bp_status st, const std::string &msg) { return fail(h, st, msg); }
+bp_status bpg_cuda_fail(bp_ctx *h, cudaError_t e, const char *where) { return cuda_fail(h, e, where); }
+bp_status bpg_ensure_buffer(bp_ctx *h, void **p, size_t bytes, const char *what) {
+    return ensure_buffer(h, p, bytes, what);
+}
+cudaError_t bpg_issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int &count) {
+    return issue_iteration(h, mode, sched, cur, count);
+}

@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/bp.h declares; argument errors are reported without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1010_0012_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bp_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["bp_create", "bp_set_unary", "bp_set_potential", "bp_reset_messages", "bp_iterate",
+                     "bp_beliefs", "bp_backward", "bp_sync", "bp_last_error", "bp_destroy",
+                     "bp_iterate_dense"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_argument_errors_without_gpu(lib):
+    lib.bp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.POINTER(ctypes.c_void_p)]
+    lib.bp_last_error.restype = ctypes.c_char_p
+    lib.bp_last_error.argtypes = [ctypes.c_void_p]
+    out = ctypes.c_void_p(123)
+    assert lib.bp_create(0, 4, 8, 0, None, ctypes.byref(out)) == 1      # BP_ERR_ARG
+    assert out.value is None
+    assert b"W and H" in lib.bp_last_error(None)
+    assert lib.bp_create(4, 4, 1, 0, None, ctypes.byref(out)) == 1      # M < 2
+    assert lib.bp_create(4, 4, 2000, 0, None, ctypes.byref(out)) == 1   # M > 1024
+    assert lib.bp_create(4, 4, 8, 7, None, ctypes.byref(out)) == 1      # dtype
+    assert lib.bp_create(4, 4, 8, 0, None, None) == 1                   # out NULL
+    assert lib.bp_create(1 << 16, 1 << 15, 8, 0, None, ctypes.byref(out)) == 1   # too large
+    for fn in ("bp_set_unary", "bp_set_messages", "bp_get_messages"):
+        getattr(lib, fn).argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        assert getattr(lib, fn)(None, None) == 1
+    lib.bp_iterate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    assert lib.bp_iterate(None, 1, 0, 0) == 1
+    lib.bp_destroy.argtypes = [ctypes.c_void_p]
+    lib.bp_destroy(None)
+    assert lib.bp_version() > 0
+
+
+def test_binding_names_match_the_abi():
+    """The Python binding exposes one function per C entry point, same name."""
+    import ast
+    src = open(os.path.join(ROOT, "paper_1010_0012_gb300", "bp.py")).read()
+    defined = {n.name for n in ast.parse(src).body if isinstance(n, ast.FunctionDef)}
+    missing = [n for n in declared_functions() if n not in defined]
+    assert not missing, missing
