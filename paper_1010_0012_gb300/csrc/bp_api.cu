@@ -327,6 +327,7 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
         BP_CK(h, cudaStreamSynchronize(h->stream));
     }
     if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
+    h->tc_ready = false;
     h->have_potential = true;
     h->recorded = false;
     clear_graphs(h);

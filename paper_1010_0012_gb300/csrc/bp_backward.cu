@@ -4,6 +4,7 @@
 #include "bp_ctx.h"
 
 void bpg_free_extras(bp_ctx *h) {
+    bpg_free_tc(h);
     for (void *p : h->ckpts)
         if (p) cudaFree(p);
     h->ckpts.clear();

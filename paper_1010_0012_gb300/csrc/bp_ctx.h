@@ -78,6 +78,7 @@ struct bp_ctx {
     void *tc_a = nullptr;           // packed h rows, bf16 [4*H*W][Mp]
     void *tc_b = nullptr;           // F^T, bf16 [Mp][Mp]
     void *tc_z = nullptr;
+    void *tc_maps = nullptr;        // host-side tensor maps (dense_tc.cu)
     bool tc_ready = false;
 };
 
@@ -92,6 +93,7 @@ cudaError_t bpg_issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int &c
 bp_status bpg_record_forward(bp_ctx *h, int n_iters);   // bp_backward.cu
 void bpg_free_extras(bp_ctx *h);                         // bp_backward.cu
 bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters);  // dense_tc.cu
+void bpg_free_tc(bp_ctx *h);                             // dense_tc.cu
 
 namespace bpg {
 cudaError_t launch_domain_convert(float *planes, long long rows, int M, int Mp, int to_log, cudaStream_t s);

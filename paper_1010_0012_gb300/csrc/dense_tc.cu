@@ -1,9 +1,462 @@
-// Dense O(M^2) sum-product baseline on the tensor cores.
+// Dense O(M^2) sum-product baseline (Eq. 2) as a tensor-core GEMM.
+//
+// One synchronous iteration is two kernels:
+//   hpack:  for every node, the four products h of Eq. 5 (unary times the
+//           other incoming messages), rounded to BF16 and written as row
+//           (s, r', c') of A = [4 H W][Mp], the row of the message slot they
+//           feed (A's rows are the message planes' rows);
+//   gemm:   D = A F (A: rows x K=Mp, F: K x N=Mp, BF16 operands, FP32
+//           accumulation), each row divided by its sum (the normalisation
+//           after Eq. 2) and stored as FP32 straight into the message planes.
+//
+// The GEMM is a persistent tcgen05 kernel: one CTA per SM; warp 0 streams
+// 128-row tiles of A with TMA (128-byte swizzle) into a 4-stage ring, warp 1
+// owns the tensor memory and issues tcgen05.mma (M = 128, N = Mp, K = 16 per
+// instruction) into one of two TMEM accumulators, warps 2-5 drain the other
+// accumulator with tcgen05.ld, normalise each row in registers and store it.
+// F^T (the B operand, Mp x Mp BF16) stays resident in shared memory.  Every
+// mbarrier wait is bounded by a 2 s timer; on expiry the kernel records an
+// error code in the handle's status word, drains its own copies and MMAs,
+// frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <vector>
 
 #include "bp_ctx.h"
 
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kBlockK = 64;            // BF16 elements in one 128-byte swizzle row
+constexpr int kStages = 4;
+constexpr int kThreads = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+// ---------------------------------------------------------------- PTX glue ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete; false on time-out or when
+// another role has given up (abort flag).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (abort_flag && *abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4)      // start address / 16
+           | ((uint64_t)1 << 16)                    // leading byte offset (unused with this swizzle)
+           | ((uint64_t)(1024 >> 4) << 32)          // stride byte offset: one 8-row group
+           | ((uint64_t)1 << 46)                    // descriptor version
+           | ((uint64_t)2 << 61);                   // 128-byte swizzle
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int MP>
+struct TcCfg {
+    static constexpr int KB = MP / kBlockK;
+    static constexpr uint32_t kAStage = (uint32_t)kTileM * MP * 2;
+    static constexpr uint32_t kBBytes = (uint32_t)MP * MP * 2;
+    static constexpr uint32_t kTmemCols = 2 * MP;   // two accumulators
+    static constexpr size_t kSmem = 1024 + kBBytes + kStages * kAStage + 256;
+};
+
+template <int MP>
+__global__ void __launch_bounds__(kThreads, 1)
+dense_tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+                     float *__restrict__ out, long long rows, int *status) {
+    using Cfg = TcCfg<MP>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sB = smem;
+    uint8_t *sA = smem + Cfg::kBBytes;
+    uint64_t *bars = (uint64_t *)(sA + kStages * Cfg::kAStage);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + kStages;
+    uint64_t *b_full = bars + 2 * kStages;
+    uint64_t *acc_full = b_full + 1;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long n_tiles = (rows + kTileM - 1) / kTileM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(b_full, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        int issued_phase[kStages];
+        for (int s = 0; s < kStages; ++s) issued_phase[s] = -1;
+        mbar_expect_tx(b_full, Cfg::kBBytes);
+        for (int kb = 0; kb < Cfg::KB; ++kb) tma_load_2d(sB + kb * MP * 128, &tmap_b, b_full, kb * kBlockK, 0);
+        long long i = 0;
+        for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+            const int s = (int)(i % kStages);
+            const uint32_t ph = (uint32_t)((i / kStages) & 1);
+            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                *abort_flag = 1;
+                atomicExch(status, 101);
+                break;
+            }
+            mbar_expect_tx(&full[s], Cfg::kAStage);
+            for (int kb = 0; kb < Cfg::KB; ++kb)
+                tma_load_2d(sA + s * Cfg::kAStage + kb * kTileM * 128, &tmap_a, &full[s], kb * kBlockK,
+                            (int)(t * kTileM));
+            issued_phase[s] = (int)ph;
+        }
+        // drain: every copy this thread issued has landed before shared memory goes away
+        mbar_wait(b_full, 0, nullptr);
+        for (int s = 0; s < kStages; ++s)
+            if (issued_phase[s] >= 0) mbar_wait(&full[s], (uint32_t)issued_phase[s], nullptr);
+    } else if (warp == 1 && lane == 0) {
+        // --------------------------------------------------------- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(kTileM, MP);
+        bool ok = mbar_wait(b_full, 0, abort_flag);
+        long long i = 0;
+        int last_acc = -1;
+        uint32_t last_aph = 0;
+        if (ok) {
+            for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+                const int s = (int)(i % kStages);
+                const uint32_t ph = (uint32_t)((i / kStages) & 1);
+                const int acc = (int)(i & 1);
+                const uint32_t aph = (uint32_t)((i >> 1) & 1);
+                if (!mbar_wait(&acc_empty[acc], aph ^ 1, abort_flag) || !mbar_wait(&full[s], ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + s * Cfg::kAStage);
+                const uint32_t b0 = smem_u32(sB);
+#pragma unroll
+                for (int kb = 0; kb < Cfg::KB; ++kb)
+#pragma unroll
+                    for (int k = 0; k < kBlockK / 16; ++k)
+                        umma_bf16(tmem_base + (uint32_t)(acc * MP), sw128_desc(a0 + kb * kTileM * 128 + k * 32),
+                                  sw128_desc(b0 + kb * MP * 128 + k * 32), idesc, (kb | k) != 0);
+                umma_commit(&empty[s]);
+                umma_commit(&acc_full[acc]);
+                last_acc = acc;
+                last_aph = aph;
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(status, 102);
+        }
+        // drain: the MMAs this thread issued have completed
+        if (last_acc >= 0) mbar_wait(&acc_full[last_acc], last_aph, nullptr);
+    } else if (warp >= 2) {
+        // ----------------------------------------------------------- epilogue
+        const int quad = warp & 3;                // TMEM lanes [32 quad, 32 quad + 32)
+        const int row_in_tile = quad * 32 + lane;
+        long long i = 0;
+        for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+            const int acc = (int)(i & 1);
+            const uint32_t aph = (uint32_t)((i >> 1) & 1);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], aph, abort_flag));
+            if (!ok) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    atomicExch(status, 103);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * MP);
+            float v[32];
+            float z = 0.f;
+#pragma unroll
+            for (int c = 0; c < MP / 32; ++c) {
+                tmem_ld32(taddr + c * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) z += v[j];
+            }
+            const float inv = z > 0.f ? 1.f / z : 0.f;
+            const long long grow = t * kTileM + row_in_tile;
+#pragma unroll
+            for (int c = 0; c < MP / 32; ++c) {
+                tmem_ld32(taddr + c * 32, v);
+                if (grow < rows) {
+                    float4 *dst = reinterpret_cast<float4 *>(out + grow * MP + c * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(v[4 * j] * inv, v[4 * j + 1] * inv, v[4 * j + 2] * inv, v[4 * j + 3] * inv);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+// h of Eq. 5 for the four outgoing messages of every node, as BF16 rows of A.
+// One thread per (node, 4 labels).
+__global__ void hpack_kernel(const float *__restrict__ g, const float *__restrict__ in, __nv_bfloat16 *__restrict__ A,
+                             bpg::GridDims d) {
+    const int chunks = d.Mp / 4;
+    const long long n = (long long)d.W * d.H * chunks;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long node = idx / chunks;
+        const int ch = (int)(idx - node * chunks);
+        const int r = (int)(node / d.W), c = (int)(node - (long long)r * d.W);
+        const bool has[4] = {c > 0, c < d.W - 1, r > 0, r < d.H - 1};
+        const long long off = node * d.Mp + ch * 4;
+        const float4 gv = __ldg(reinterpret_cast<const float4 *>(g + off));
+        float4 m[4];
+        for (int s = 0; s < 4; ++s)
+            m[s] = has[s] ? __ldg(reinterpret_cast<const float4 *>(in + s * d.plane + off)) : make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (!has[t]) continue;
+            float4 h = gv;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (s == t) continue;
+                h.x *= m[s].x; h.y *= m[s].y; h.z *= m[s].z; h.w *= m[s].w;
+            }
+            const int dr = (t == 2) ? -1 : (t == 3) ? 1 : 0;
+            const int dc = (t == 0) ? -1 : (t == 1) ? 1 : 0;
+            const long long row = (long long)(t ^ 1) * d.W * d.H + (long long)(r + dr) * d.W + (c + dc);
+            __nv_bfloat162 lo = __floats2bfloat162_rn(h.x, h.y);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(h.z, h.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<uint32_t *>(&lo);
+            pk.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(A + row * d.Mp + ch * 4) = pk;
+        }
+    }
+}
+
+__global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][cols] matrix, box [box_rows][64].
+bool make_map(CUtensorMap *map, const void *base, unsigned long long rows, unsigned long long cols, unsigned box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBlockK, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcState {
+    CUtensorMap map_a, map_b;
+};
+
+template <int MP>
+cudaError_t launch_gemm(const TcState &st, float *out, long long rows, int *status, cudaStream_t s) {
+    using Cfg = TcCfg<MP>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(dense_tc_gemm_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long tiles = (rows + kTileM - 1) / kTileM;
+    int grid = bpg::device_sm_count();
+    if (grid > tiles) grid = (int)tiles;
+    dense_tc_gemm_kernel<MP><<<grid, kThreads, Cfg::kSmem, s>>>(st.map_a, st.map_b, out, rows, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters) {
-    (void)n_iters;
-    return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_iterate_dense: tensor-core baseline not available in this build");
+    if (h->Mp != 64 && h->Mp != 128)
+        return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_iterate_dense: the tensor-core baseline serves 33 <= M <= 128");
+    const long long rows = 4LL * h->W * h->H;
+    const int Mp = h->Mp;
+    if (!h->tc_ready) {
+        bpg_free_tc(h);
+        if (bp_status st = bpg_ensure_buffer(h, &h->tc_a, (size_t)rows * Mp * 2, "tensor-core A")) return st;
+        if (bp_status st = bpg_ensure_buffer(h, &h->tc_b, (size_t)Mp * Mp * 2, "tensor-core B")) return st;
+        if (bp_status st = bpg_ensure_buffer(h, &h->tc_z, (size_t)Mp * Mp * 4 + sizeof(TcState) + 64, "tensor-core maps"))
+            return st;
+        // B[x_j][x_i] = f(x_i, x_j) (F transposed: K = x_i contiguous), zero outside M
+        std::vector<float> Bt((size_t)Mp * Mp, 0.f);
+        for (int xj = 0; xj < h->M; ++xj)
+            for (int xi = 0; xi < h->M; ++xi) {
+                const int d = xi - xj;
+                Bt[(size_t)xj * Mp + xi] = (d >= -h->T && d <= h->T) ? h->tablef[d + h->T] : h->fbarf;
+            }
+        cudaError_t e = cudaMemcpyAsync(h->tc_z, Bt.data(), Bt.size() * 4, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return bpg_cuda_fail(h, e, "tensor-core B upload");
+        to_bf16_kernel<<<64, 256, 0, h->stream>>>((const float *)h->tc_z, (__nv_bfloat16 *)h->tc_b, Mp * Mp);
+        e = cudaMemsetAsync(h->tc_a, 0, (size_t)rows * Mp * 2, h->stream);
+        if (e != cudaSuccess) return bpg_cuda_fail(h, e, "tensor-core A clear");
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return bpg_cuda_fail(h, e, "tensor-core setup");
+        h->launches += 1;
+        TcState *stt = new TcState();
+        if (!make_map(&stt->map_a, h->tc_a, (unsigned long long)rows, (unsigned long long)Mp, kTileM) ||
+            !make_map(&stt->map_b, h->tc_b, (unsigned long long)Mp, (unsigned long long)Mp, (unsigned)Mp)) {
+            delete stt;
+            return bpg_fail(h, BP_ERR_CUDA, "bp_iterate_dense: cuTensorMapEncodeTiled failed");
+        }
+        h->tc_maps = stt;
+        h->tc_ready = true;
+    }
+    const TcState &st = *(const TcState *)h->tc_maps;
+    for (int it = 0; it < n_iters; ++it) {
+        const long long n = (long long)h->W * h->H * (Mp / 4);
+        hpack_kernel<<<bpg::grid_for(n, 256), 256, 0, h->stream>>>((const float *)h->unary, (const float *)h->msg[h->cur],
+                                                                   (__nv_bfloat16 *)h->tc_a, h->dims);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return bpg_cuda_fail(h, e, "hpack launch");
+        e = Mp == 128 ? launch_gemm<128>(st, (float *)h->msg[h->cur ^ 1], rows, h->d_status, h->stream)
+                      : launch_gemm<64>(st, (float *)h->msg[h->cur ^ 1], rows, h->d_status, h->stream);
+        if (e != cudaSuccess) return bpg_cuda_fail(h, e, "tensor-core GEMM launch");
+        h->launches += 2;
+        h->cur ^= 1;
+    }
+    return BP_OK;
+}
+
+void bpg_free_tc(bp_ctx *h) {
+    delete (TcState *)h->tc_maps;
+    h->tc_maps = nullptr;
 }
