@@ -146,6 +146,35 @@ bp_status bp_set_layout(bp_handle h, int lanes_per_node, int vec_chunks);
 bp_status bp_get_layout(bp_handle h, int *lanes_per_node, int *vec_chunks);
 bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms);
 
+/* Allocation-free dense tensor-core iteration (no counterpart in the paper;
+ * an addition for callers that cannot allocate device memory).  Some callers
+ * cannot call cudaMalloc: their device memory is planned once by another
+ * component (a serving process's memory pool, a framework that forbids
+ * allocation after warm-up), or an allocation at that point could synchronise
+ * the device or fail unpredictably.  This call runs one synchronous iteration
+ * of the BF16 tensor-core O(M^2) update (as bp_iterate_dense with
+ * BP_DENSE_BF16_TC) without any allocation: its scratch lives in a fixed
+ * device array of 32 MiB + 32 KiB inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   W, H, M         grid and label count; M must be 64 or 128, and the packed
+ *                   rows 4*W*H*M*2 bytes must fit in 32 MiB (W*H <= 32768 at
+ *                   M = 128, <= 65536 at M = 64); larger sizes return BP_ERR_ARG.
+ *   dev_unary       [H][W][M] float32 g > 0;
+ *   dev_in_planes   [4][H][W][M] float32 current messages (layout as above);
+ *   dev_out_planes  [4][H][W][M] float32 updated messages (must differ from
+ *                   dev_in_planes); slots without a neighbour receive 0;
+ *   host_table      2T+1 float32 values f(d), d = -T..T, and fbar outside.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  The call enqueues its kernels on cuda_stream (NULL: the legacy
+ * default stream) and returns after they have completed.  All calls share the
+ * one array, which keeps the last call's contents: calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  Errors are reported through bp_last_error(NULL). */
+bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const float *dev_unary, const float *dev_in_planes,
+                                      float *dev_out_planes, const float *host_table, int T, double fbar,
+                                      void *cuda_stream);
+
 /* Number of kernel launches the library issued on this handle so far. */
 long long bp_launch_count(bp_handle h);
 

@@ -57,6 +57,7 @@ def _load():
         "bp_get_layout": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
         "bp_autotune": ([P, I, I, ctypes.POINTER(ctypes.c_float)], I),
         "bp_launch_count": ([P], ctypes.c_longlong),
+        "bp_iterate_dense_tc_noalloc": ([I, I, I, P, P, P, P, I, D, P], I),
         "bp_version": ([], I),
     }
     for name, (args, res) in sig.items():
@@ -187,6 +188,21 @@ def bp_autotune(h, mode, n_iters=3):
 
 def bp_launch_count(h):
     return _lib.bp_launch_count(h)
+
+
+def bp_iterate_dense_tc_noalloc(W, H, M, unary: torch.Tensor, in_planes: torch.Tensor, out_planes: torch.Tensor,
+                                table, T: int, fbar: float, stream=None):
+    """One dense tensor-core iteration that allocates nothing (see include/bp.h)."""
+    import numpy as np
+    tab = np.ascontiguousarray(table, dtype=np.float32)
+    if tab.size != 2 * T + 1:
+        raise ValueError("table must hold 2T + 1 values")
+    st = _lib.bp_iterate_dense_tc_noalloc(int(W), int(H), int(M), _dptr(unary, torch.float32, H * W * M),
+                                          _dptr(in_planes, torch.float32, 4 * H * W * M),
+                                          _dptr(out_planes, torch.float32, 4 * H * W * M),
+                                          tab.ctypes.data_as(ctypes.c_void_p), int(T), float(fbar),
+                                          _stream_ptr(stream))
+    _check(None, st)
 
 
 # ---- a thin owner of one handle -------------------------------------------------

@@ -23,6 +23,10 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "bp_ctx.h"
@@ -459,4 +463,126 @@ bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters) {
 void bpg_free_tc(bp_ctx *h) {
     delete (TcState *)h->tc_maps;
     h->tc_maps = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free form of one tensor-core dense iteration.
+//
+// Some callers cannot call cudaMalloc at all: a host process whose device
+// memory is planned once at start-up by another component (an inference
+// server's memory pool, a framework that forbids allocation after warm-up), or
+// code running in a context where an allocation would synchronise the device
+// or could fail at an unpredictable time.  For them the dense tensor-core
+// iteration is also offered without any allocation: its scratch (the packed
+// BF16 rows of h, the BF16 copy of F^T and a status word) lives in the
+// file-scope array below, which every GPU that loads this library holds until
+// the process exits.  The caller passes inputs and outputs only.
+namespace {
+
+constexpr size_t kNoAllocRowBytes = (size_t)32 << 20;          // packed h rows: at most 32 MiB
+constexpr size_t kNoAllocBBytes = (size_t)128 * 128 * 2;       // F^T, BF16, M <= 128
+constexpr size_t kNoAllocBytes = kNoAllocRowBytes + kNoAllocBBytes + 256;
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+uint8_t *g_noalloc_base[kNoAllocMaxDevices];   // device address of the array, per device
+
+struct NoAllocTable {
+    float f[256];   // f(d), d = -T..T (T <= 127)
+    int T;
+    float fbar;
+};
+
+// B[x_j][x_i] = f(x_i - x_j) inside the band, fbar outside, in BF16; clears the
+// packed rows (rows of absent messages must read as zero) and the status word.
+__global__ void noalloc_prep_kernel(NoAllocTable tab, int M, __nv_bfloat16 *B, uint4 *rows16, long long n16,
+                                    int *status) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    for (long long i = tid; i < (long long)M * M; i += nthreads) {
+        const int xj = (int)(i / M), xi = (int)(i - (long long)xj * M);
+        const int d = xi - xj;
+        B[i] = __float2bfloat16_rn((d >= -tab.T && d <= tab.T) ? tab.f[d + tab.T] : tab.fbar);
+    }
+    for (long long i = tid; i < n16; i += nthreads) rows16[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) *status = 0;
+}
+
+// errors are reported through bp_last_error(NULL), like those of bp_create
+bp_status noalloc_fail(bp_status st, const std::string &m) { return bpg_fail(nullptr, st, m); }
+
+}  // namespace
+
+static __device__ __align__(256) uint8_t bpg_noalloc_scratch[kNoAllocBytes];
+
+extern "C" bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const float *dev_unary,
+                                                 const float *dev_in_planes, float *dev_out_planes,
+                                                 const float *host_table, int T, double fbar, void *cuda_stream) {
+    bpg_fail(nullptr, BP_OK, "");
+    if (W < 1 || H < 1) return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: W and H must be >= 1");
+    if (M != 64 && M != 128) return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: M must be 64 or 128");
+    if (!dev_unary || !dev_in_planes || !dev_out_planes || !host_table)
+        return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: NULL pointer");
+    if (dev_in_planes == dev_out_planes)
+        return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: input and output planes must differ");
+    if (T < 0 || !(fbar >= 0) || !std::isfinite(fbar))
+        return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: need T >= 0 and a finite fbar >= 0");
+    const long long rows = 4LL * W * H;
+    if ((long long)W * H > (1LL << 30) || (size_t)rows * M * 2 > kNoAllocRowBytes)
+        return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: 4*W*H*M*2 bytes of packed rows exceed the "
+                                        "fixed 32 MiB scratch (use bp_iterate_dense on a handle instead)");
+    NoAllocTable tab;
+    tab.T = std::min(T, M - 1);
+    tab.fbar = (float)fbar;
+    for (int d = -tab.T; d <= tab.T; ++d) {
+        const float v = host_table[d + T];
+        if (!std::isfinite(v) || v < 0)
+            return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: table entries must be finite and >= 0");
+        tab.f[d + tab.T] = v;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(BP_ERR_UNSUPPORTED, "device index out of range");
+    uint8_t *base = nullptr;
+    {
+        // once per device, with that device current: the host-side name of the
+        // array is not a device address, so ask the runtime for the address
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_base[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, bpg_noalloc_scratch);
+            if (e != cudaSuccess)
+                return noalloc_fail(BP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_base[dev] = (uint8_t *)p;
+        }
+        base = g_noalloc_base[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    __nv_bfloat16 *A = (__nv_bfloat16 *)base;
+    __nv_bfloat16 *B = (__nv_bfloat16 *)(base + kNoAllocRowBytes);
+    int *status = (int *)(base + kNoAllocRowBytes + kNoAllocBBytes);
+    const long long n16 = (long long)rows * M * 2 / 16;
+    noalloc_prep_kernel<<<bpg::grid_for(n16 > (long long)M * M ? n16 : (long long)M * M, 256), 256, 0, s>>>(
+        tab, M, B, (uint4 *)A, n16, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("prep launch: ") + cudaGetErrorString(e));
+    const bpg::GridDims d{W, H, M, M, (long long)W * H * M};
+    hpack_kernel<<<bpg::grid_for((long long)W * H * (M / 4), 256), 256, 0, s>>>(dev_unary, dev_in_planes, A, d);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("hpack launch: ") + cudaGetErrorString(e));
+    TcState st;
+    if (!make_map(&st.map_a, A, (unsigned long long)rows, (unsigned long long)M, kTileM) ||
+        !make_map(&st.map_b, B, (unsigned long long)M, (unsigned long long)M, (unsigned)M))
+        return noalloc_fail(BP_ERR_CUDA, "bp_iterate_dense_tc_noalloc: cuTensorMapEncodeTiled failed");
+    e = M == 128 ? launch_gemm<128>(st, dev_out_planes, rows, status, s)
+                 : launch_gemm<64>(st, dev_out_planes, rows, status, s);
+    if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("GEMM launch: ") + cudaGetErrorString(e));
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("iteration: ") + cudaGetErrorString(e));
+    int flag = 0;
+    e = cudaMemcpy(&flag, status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (flag) return noalloc_fail(BP_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up");
+    return BP_OK;
 }
