@@ -80,6 +80,10 @@ bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_h
  * BP_F32, int32 energies E_u >= 0 for BP_I32.  Copied into the handle. */
 bp_status bp_set_unary(bp_handle h, const void *dev_unary);
 
+/* The same unary given as log g (BP_F32 only): dev_logg [H][W][M] float32.
+ * Log-domain runs use these values as they are (no round trip through g). */
+bp_status bp_set_unary_log(bp_handle h, const float *dev_logg);
+
 /* Pairwise potential with the sparse compatibility property (Sec. 4):
  * host_table[d + T] = f(d), d = x_i - x_j (sender minus receiver label),
  * -T <= d <= T; every pair with |d| > T has the value fbar.

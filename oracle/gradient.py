@@ -129,3 +129,60 @@ def finite_difference(cost, d_gt, alpha, fbar, beta, T, n_iters, schedule="sync"
         lm = loss_value(cost, d_gt, dn["alpha"], dn["fbar"], dn["beta"], T, n_iters, schedule)
         out["d_" + k] = (lp - lm) / (2 * h)
     return out
+
+
+def _pair_matrix_from_table(table, fbar, T, M):
+    """F[x_i, x_j] = table[x_i - x_j + T] for |x_i - x_j| <= T, fbar otherwise."""
+    xi = torch.arange(M)[:, None]
+    xj = torch.arange(M)[None, :]
+    d = xi - xj
+    inside = d.abs() <= T
+    idx = (d + T).clamp(0, 2 * T)
+    return torch.where(inside, table[idx], fbar * torch.ones((M, M), dtype=_DT))
+
+
+def reference_gradient_table(cost, d_gt, table, fbar, beta, T, n_iters, schedule="sync"):
+    """Exact FP64 gradient with the band values f(d) themselves as parameters:
+    dict with loss, d_table [2T+1], d_fbar, d_logg."""
+    cost_t = torch.as_tensor(np.asarray(cost), dtype=_DT)
+    tab = torch.tensor(np.asarray(table, dtype=np.float64), requires_grad=True)
+    fb = torch.tensor(float(fbar), dtype=_DT, requires_grad=True)
+    logg = (-float(beta) * cost_t).detach().requires_grad_(True)
+    H, W, M = logg.shape
+    F = _pair_matrix_from_table(tab, fb, T, M)
+    loss = _nll_with_matrix(logg, F, n_iters, d_gt, schedule)
+    d_logg, d_tab, d_fb = torch.autograd.grad(loss, [logg, tab, fb])
+    return {"loss": float(loss.detach()), "d_table": d_tab.numpy(), "d_fbar": float(d_fb),
+            "d_logg": d_logg.numpy()}
+
+
+def _nll_with_matrix(logg, F, n_iters, d_gt, schedule):
+    """The same unrolled dense iteration as sum_product_planes, for a given F."""
+    H, W, M = logg.shape
+    g = torch.exp(logg)
+    present = _present(H, W)
+    ones = torch.ones((H, W, M), dtype=_DT)
+    planes = torch.where(present, torch.full((4, H, W, M), 1.0 / M, dtype=_DT), 1.0)
+    parity = (torch.arange(H)[:, None] + torch.arange(W)[None, :]) % 2
+
+    def all_new(P):
+        P0, P1, P2, P3 = P[0], P[1], P[2], P[3]
+        to_right = _normalise((g * P0 * P2 * P3) @ F)
+        to_left = _normalise((g * P1 * P2 * P3) @ F)
+        to_down = _normalise((g * P0 * P1 * P2) @ F)
+        to_up = _normalise((g * P0 * P1 * P3) @ F)
+        return torch.stack([torch.cat([ones[:, :1], to_right[:, :-1]], dim=1),
+                            torch.cat([to_left[:, 1:], ones[:, -1:]], dim=1),
+                            torch.cat([ones[:1], to_down[:-1]], dim=0),
+                            torch.cat([to_up[1:], ones[-1:]], dim=0)])
+
+    for _ in range(n_iters):
+        if schedule == "sync":
+            planes = all_new(planes)
+        else:
+            for p in (0, 1):
+                planes = torch.where((parity == 1 - p)[None, ..., None], all_new(planes), planes)
+    b = g * planes.prod(dim=0)
+    bel = b / b.sum(-1, keepdim=True)
+    idx = torch.as_tensor(np.asarray(d_gt), dtype=torch.long)[..., None]
+    return -torch.log(torch.gather(bel, -1, idx)).sum()

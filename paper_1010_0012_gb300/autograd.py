@@ -1,0 +1,68 @@
+"""torch.autograd.Function around the recorded log-domain forward and the
+hand-written adjoint of the library (bp_iterate with BP_SUM|BP_LOG|BP_RECORD,
+bp_beliefs, bp_backward).
+
+BPFunction maps (log g, band table f(d), fbar) to the normalised log-beliefs
+after K unrolled synchronous sum-product iterations.  Its backward calls
+bp_backward, which recomputes each checkpoint segment and runs the adjoint
+kernel; the parameter gradients (dL/df(d), dL/dfbar) come back in FP64.
+The library does all of the BP arithmetic; this module only moves tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import bp
+
+
+class BPFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, logg, table, fbar, grid, T, n_iters, every):
+        if logg.dtype != torch.float32 or not logg.is_cuda:
+            raise TypeError("logg must be a float32 CUDA tensor [H][W][M]")
+        h = grid.h
+        bp.bp_set_unary_log(h, logg.detach().contiguous())
+        bp.bp_set_potential(h, table.detach().cpu().numpy().astype(np.float32), T, float(fbar), bp.BP_F32)
+        bp.bp_set_checkpoint_interval(h, every)
+        bp.bp_reset_messages(h)
+        bp.bp_iterate(h, n_iters, bp.BP_SUM | bp.BP_LOG | bp.BP_RECORD, bp.BP_SYNC)
+        logb = torch.empty_like(logg)
+        bp.bp_beliefs(h, logb)
+        bp.bp_sync(h)
+        ctx.grid = grid
+        ctx.T = T
+        ctx.table_meta = (table.dtype, table.device)
+        ctx.fbar_meta = (fbar.dtype, fbar.device) if isinstance(fbar, torch.Tensor) else None
+        return logb
+
+    @staticmethod
+    def backward(ctx, dlogb):
+        dlogg = torch.empty_like(dlogb)
+        dtab, dfbar = bp.bp_backward(ctx.grid.h, dlogb.detach().float().contiguous(), dlogg, 2 * ctx.T + 1)
+        tdt, tdev = ctx.table_meta
+        g_tab = torch.as_tensor(dtab, dtype=torch.float64).to(device=tdev, dtype=tdt)
+        g_fbar = None
+        if ctx.fbar_meta is not None:
+            g_fbar = torch.tensor(dfbar, dtype=torch.float64).to(device=ctx.fbar_meta[1], dtype=ctx.fbar_meta[0])
+        return dlogg, g_tab, g_fbar, None, None, None, None
+
+
+def log_beliefs(logg, table, fbar, grid, T, n_iters, every=5):
+    """Normalised log-beliefs after n_iters log-domain iterations (differentiable
+    in logg, table and fbar)."""
+    return BPFunction.apply(logg, table, fbar, grid, T, n_iters, every)
+
+
+def stereo_nll(cost, d_gt, alpha, fbar, beta, T, n_iters, grid, every=5):
+    """-sum_i log b_i(x_i*) of the stereo model (Sec. 6) with parameters
+    alpha, fbar, beta as tensors: log g = -beta cost, f(d) = exp(-alpha |d|)
+    for |d| <= T and fbar outside.  Autograd's chain rule maps the library's
+    dL/d log g, dL/df(d), dL/dfbar to dL/d beta, d alpha, d fbar."""
+    dev = cost.device
+    logg = -beta.to(dev) * cost
+    d = torch.arange(-T, T + 1, dtype=torch.float32, device=alpha.device).abs()
+    table = torch.exp(-alpha * d)
+    logb = log_beliefs(logg.float().contiguous(), table, fbar, grid, T, n_iters, every)
+    idx = torch.as_tensor(d_gt, dtype=torch.long, device=dev)[..., None]
+    return -torch.gather(logb, -1, idx).sum()

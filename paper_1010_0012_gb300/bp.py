@@ -41,6 +41,7 @@ def _load():
     sig = {
         "bp_create": ([I, I, I, I, P, ctypes.POINTER(P)], I),
         "bp_set_unary": ([P, P], I),
+        "bp_set_unary_log": ([P, P], I),
         "bp_set_potential": ([P, P, I, D], I),
         "bp_reset_messages": ([P], I),
         "bp_iterate": ([P, I, I, I], I),
@@ -112,6 +113,10 @@ def bp_destroy(h):
 
 def bp_set_unary(h, unary: torch.Tensor, dtype):
     _check(h, _lib.bp_set_unary(h, _dptr(unary, torch.float32 if dtype == BP_F32 else torch.int32)))
+
+
+def bp_set_unary_log(h, logg: torch.Tensor):
+    _check(h, _lib.bp_set_unary_log(h, _dptr(logg, torch.float32)))
 
 
 def bp_set_potential(h, table, T: int, fbar: float, dtype):

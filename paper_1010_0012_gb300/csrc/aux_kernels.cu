@@ -272,7 +272,8 @@ __global__ void pad_f32_kernel(const float *src, float *dst, long long nodes, in
         float v = 0.f;
         if (x < M) {
             v = src[node * M + x];
-            if (lg) v = logf(v);
+            if (lg == 1) v = logf(v);
+            else if (lg == 2) v = expf(v);
         }
         dst[i] = v;
     }

@@ -1,0 +1,287 @@
+// Reverse mode of the log-domain O(mM) sum-product update.
+//
+// Forward, for the message from node i to its neighbour j (Eq. 5, Eq. 7, with
+// the log-domain shift A = max_x a(x), which leaves the result unchanged):
+//   a(x)   = log g_i(x) + sum_{k != j} l_ki(x),   h(x) = exp(a(x) - A)
+//   S      = sum_x h(x),  B(x_j) = sum_{|d|<=T} w(d) h(x_j + d),  w(d) = f(d) - fbar
+//   u(x_j) = B(x_j) + fbar S,  Z = sum_x u(x),  l_ij(x_j) = log u(x_j) - log Z
+// Reverse, given delta(x_j) = dL/dl_ij(x_j):
+//   nu(x_j)   = delta(x_j) / u(x_j) - (sum_x delta(x)) / Z            (= dL/du)
+//   dh(x_i)   = sum_{|e|<=T} w(-e) nu(x_i + e) + fbar sum_x nu(x)      (band transposed: O(mM))
+//   da(x_i)   = dh(x_i) h(x_i)   -> dL/d log g_i and dL/d l_ki for every k != j
+//   dw(d)    += sum_{x_j} nu(x_j) h(x_j + d)                           (= dL/df(d))
+//   dfbar    += S sum_x nu(x) - sum_d dw(d)   (fbar enters u directly and through w)
+// The common factor exp(A) of h, u, Z and nu cancels in every product above.
+//
+// One kernel launch reverses one synchronous iteration for every node; the
+// per-block sums of dw and dfbar go to a scratch row per (iteration, block),
+// reduced over all edges and iterations in FP64 at the end.
+#include <cuda_runtime.h>
+
+#include "band_dispatch.cuh"
+#include "band_fast.cuh"
+#include "bp_adjoint.h"
+
+namespace bpg {
+
+template <int L, int C, int T>
+__global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs a) {
+    constexpr int V = 4 * C;
+    constexpr int GPB = kBlock / L;
+    constexpr int NP = 2 * T + 2;      // dw(-T..T), dfbar
+    const int q = threadIdx.x & (L - 1);
+    const int grp = threadIdx.x / L;
+    const int W = a.d.W, H = a.d.H, M = a.d.M, Mp = a.d.Mp;
+    const long long plane = a.d.plane;
+
+    float w[2 * T + 1];
+#pragma unroll
+    for (int i = 0; i < 2 * T + 1; ++i) w[i] = a.w[i];
+    const float fbar = a.fbar;
+    float cz[V];
+    bool lab_ok[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int x = q * V + k;
+        float cx = 0.f;
+#pragma unroll
+        for (int d = -T; d <= T; ++d)
+            if (x - d >= 0 && x - d < M) cx += w[d + T];
+        lab_ok[k] = x < M;
+        cz[k] = lab_ok[k] ? cx + (float)M * fbar : 0.f;
+    }
+
+    float pacc[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) pacc[i] = 0.f;
+
+    const int nslots = W * H;
+    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
+        int r, c;
+        const bool valid = slot_node(base + grp, nslots, W, -1, r, c);
+        const long long off = ((long long)r * W + c) * Mp + q * V;
+        const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
+
+        float gam[V], l[4][V];
+        if (valid) ld_vec<V>(gam, a.logg + off); else fill_vec<V>(gam, 0.f);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (has[s]) ld_vec<V>(l[s], a.ell + s * plane + off);
+            else fill_vec<V>(l[s], 0.f);
+        }
+        float dl[4][V], dg[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            dg[k] = 0.f;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) dl[s][k] = 0.f;
+        }
+
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            // forward recompute of the message towards neighbour t
+            float h[V];
+            float amax = kLogNone;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                float s = gam[k];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u != t) s += l[u][k];
+                h[k] = lab_ok[k] ? s : kLogNone;
+                amax = fmaxf(amax, h[k]);
+            }
+            amax = group_max<L>(amax);
+            float S = 0.f, Z = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                h[k] = lab_ok[k] ? expf(h[k] - amax) : 0.f;
+                S += h[k];
+                Z = fmaf(h[k], cz[k], Z);
+            }
+            S = group_sum<L>(S);
+            Z = group_sum<L>(Z);
+            float win[V + 2 * T];
+            band_window<L, V, T, float>(win, h, q, 0.f);
+
+            // adjoint of the stored message
+            float del[V];
+            if (has[t]) ld_vec<V>(del, a.lam_next + out_offset(t, r, c, W, plane, Mp) + q * V);
+            else fill_vec<V>(del, 0.f);
+            float nd = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                del[k] = lab_ok[k] ? del[k] : 0.f;
+                nd += del[k];
+            }
+            nd = group_sum<L>(nd);
+            const float invZ = 1.f / Z;
+            float nu[V];
+            float nn = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                float u = fbar * S;
+#pragma unroll
+                for (int d = -T; d <= T; ++d) u = fmaf(w[d + T], win[T + k + d], u);
+                nu[k] = lab_ok[k] ? del[k] / u - nd * invZ : 0.f;
+                nn += nu[k];
+            }
+            nn = group_sum<L>(nn);
+
+            // dh through the transposed band, then da = dh * h
+            float nwin[V + 2 * T];
+            band_window<L, V, T, float>(nwin, nu, q, 0.f);
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                float dh = fbar * nn;
+#pragma unroll
+                for (int e = -T; e <= T; ++e) dh = fmaf(w[-e + T], nwin[T + k + e], dh);
+                const float da = lab_ok[k] ? dh * h[k] : 0.f;
+                dg[k] += da;
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    if (s != t) dl[s][k] += da;
+            }
+
+            // parameter gradients
+            float dsum = 0.f;
+#pragma unroll
+            for (int d = -T; d <= T; ++d) {
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < V; ++k) acc = fmaf(nu[k], win[T + k + d], acc);
+                pacc[d + T] += acc;
+                dsum += acc;
+            }
+            pacc[NP - 1] += (q == 0 ? nn * S : 0.f) - dsum;
+        }
+
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (has[s]) st_vec<V>(a.lam + s * plane + off, dl[s]);
+        if (valid) {
+            float acc[V];
+            ld_vec<V>(acc, a.dlogg + off);
+#pragma unroll
+            for (int k = 0; k < V; ++k) acc[k] += dg[k];
+            st_vec<V>(a.dlogg + off, acc);
+        }
+    }
+
+    // block sums of the parameter gradients -> scratch row of this block
+    __shared__ float red[kBlock / 32][NP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float v = pacc[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(BPG_FULL, v, o);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        float v = 0.f;
+        for (int k = 0; k < kBlock / 32; ++k) v += red[k][threadIdx.x];
+        a.partial[(long long)blockIdx.x * NP + threadIdx.x] = v;
+    }
+}
+
+struct AdjTag {
+    template <int L, int C, int T>
+    static const void *get() { return (const void *)band_log_adjoint_kernel<L, C, T>; }
+};
+
+int adjoint_blocks(const GridDims &d, Layout lay, int T) {
+    const void *fn = pick_kernel<AdjTag>(lay, T);
+    if (!fn) return 0;
+    const int per_block = kBlock / lay.L;
+    const long long need = ((long long)d.W * d.H + per_block - 1) / per_block;
+    long long b = (long long)device_sm_count() * blocks_per_sm(fn);
+    if (b > need) b = need;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_band_log_adjoint(const AdjArgs &a, Layout lay, int blocks, cudaStream_t s) {
+    const void *fn = pick_kernel<AdjTag>(lay, a.T);
+    if (!fn || lay.L * 4 * lay.C != a.d.Mp || blocks < 1) return cudaErrorInvalidValue;
+    void *args[] = {const_cast<AdjArgs *>(&a)};
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(kBlock), args, 0, s);
+}
+
+// ---- reverse of the beliefs (Eq. 3 in logs) ------------------------------------
+// log b(x) = a(x) - logsumexp(a), a = log g + sum of incoming l; given
+// dL/d log b, da = dlogb - softmax(a) sum_x dlogb.  da seeds dL/d log g and the
+// adjoint of every incoming message of the final state.  One warp per node.
+__global__ void beliefs_log_adjoint_kernel(const float *logg, const float *ell, const float *dlogb, GridDims d,
+                                           float *lam, float *dlogg) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int W = d.W, H = d.H, M = d.M, Mp = d.Mp;
+    for (long long node = warp; node < (long long)W * H; node += nwarps) {
+        const int r = (int)(node / W), c = (int)(node - (long long)r * W);
+        const bool has[4] = {c > 0, c < W - 1, r > 0, r < H - 1};
+        float amax = -3.0e38f, D = 0.f;
+        for (int x = lane; x < M; x += 32) {
+            float av = logg[node * Mp + x];
+            for (int s = 0; s < 4; ++s)
+                if (has[s]) av += ell[s * d.plane + node * Mp + x];
+            amax = fmaxf(amax, av);
+            D += dlogb[node * M + x];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            D += __shfl_xor_sync(0xffffffffu, D, o);
+        }
+        float Z = 0.f;
+        for (int x = lane; x < M; x += 32) {
+            float av = logg[node * Mp + x];
+            for (int s = 0; s < 4; ++s)
+                if (has[s]) av += ell[s * d.plane + node * Mp + x];
+            Z += expf(av - amax);
+        }
+        for (int o = 16; o > 0; o >>= 1) Z += __shfl_xor_sync(0xffffffffu, Z, o);
+        for (int x = lane; x < Mp; x += 32) {
+            float da = 0.f;
+            if (x < M) {
+                float av = logg[node * Mp + x];
+                for (int s = 0; s < 4; ++s)
+                    if (has[s]) av += ell[s * d.plane + node * Mp + x];
+                da = dlogb[node * M + x] - expf(av - amax) / Z * D;
+            }
+            dlogg[node * Mp + x] = da;
+            for (int s = 0; s < 4; ++s)
+                if (has[s]) lam[s * d.plane + node * Mp + x] = da;
+        }
+    }
+}
+
+cudaError_t launch_beliefs_log_adjoint(const float *logg, const float *ell, const float *dlogb, GridDims d,
+                                       float *lam, float *dlogg, cudaStream_t s) {
+    beliefs_log_adjoint_kernel<<<grid_for((long long)d.W * d.H * 32, 256), 256, 0, s>>>(logg, ell, dlogb, d, lam,
+                                                                                       dlogg);
+    return cudaGetLastError();
+}
+
+// ---- final reduction of the parameter gradients in FP64 ------------------------
+// out[j] = sum over rows of partial[row][j], rows = iterations x blocks.
+__global__ void reduce_partials_f64_kernel(const float *partial, long long rows, int np, double *out) {
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < rows; i += blockDim.x) acc += (double)partial[i * np + j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = red[0];
+}
+
+cudaError_t launch_reduce_partials_f64(const float *partial, long long rows, int np, double *out, cudaStream_t s) {
+    reduce_partials_f64_kernel<<<np, 256, 0, s>>>(partial, rows, np, out);
+    return cudaGetLastError();
+}
+
+}  // namespace bpg

@@ -273,6 +273,23 @@ bp_status bp_set_unary(bp_handle h, const void *dev_unary) {
     return BP_OK;
 }
 
+bp_status bp_set_unary_log(bp_handle h, const float *dev_logg) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary_log: NULL handle");
+    h->err.clear();
+    if (!dev_logg) return fail(h, BP_ERR_ARG, "bp_set_unary_log: NULL unary");
+    if (h->dtype != BP_F32) return fail(h, BP_ERR_ARG, "bp_set_unary_log: needs a BP_F32 handle");
+    if (bp_status st = bpg_check_device(h)) return st;
+    const long long nodes = (long long)h->W * h->H;
+    if (bp_status st = ensure_buffer(h, (void **)&h->log_unary, (size_t)nodes * h->Mp * 4, "log unary")) return st;
+    BP_CK(h, launch_pad_copy_f32(dev_logg, h->log_unary, nodes, h->M, h->Mp, 0, h->stream));
+    BP_CK(h, launch_pad_copy_f32(dev_logg, (float *)h->unary, nodes, h->M, h->Mp, 2, h->stream));
+    h->launches += 2;
+    h->have_unary = true;
+    h->log_unary_valid = true;
+    h->recorded = false;
+    return BP_OK;
+}
+
 bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fbar) {
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_potential: NULL handle");
     h->err.clear();

@@ -1,26 +1,150 @@
-// Recorded log-domain forward and its adjoint (bp_backward).
+// Recorded log-domain forward (checkpoints) and its reverse (bp_backward).
+//
+// Forward with BP_RECORD: the message state entering iterations 0, c, 2c, ...
+// is copied to a checkpoint (c = checkpoint interval).  Backward walks the
+// segments from the last to the first: it recomputes the states of a segment
+// from its checkpoint with the same forward kernel (so bit-identical to the
+// recorded run), then applies the adjoint kernel once per iteration in
+// reverse, accumulating dL/d log g and per-block sums of dL/df(d), dL/dfbar;
+// those sums are reduced over all blocks and iterations in FP64.
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "bp_adjoint.h"
 #include "bp_ctx.h"
+
+using namespace bpg;
 
 void bpg_free_extras(bp_ctx *h) {
     bpg_free_tc(h);
     for (void *p : h->ckpts)
         if (p) cudaFree(p);
     h->ckpts.clear();
-    void *bufs[] = {h->seg_buf, h->adj[0], h->adj[1], h->dtab_partial, h->tc_a, h->tc_b, h->tc_z};
+    void *bufs[] = {h->seg_buf, h->adj[0], h->adj[1], h->dtab_partial, h->tc_a, h->tc_b, h->tc_z, h->dlogg_pad,
+                    h->d_red};
     for (void *p : bufs)
         if (p) cudaFree(p);
 }
 
+#define BK_CK(h, call)                                                   \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return bpg_cuda_fail((h), e_, #call);     \
+    } while (0)
+
+static BandArgsF log_args(bp_ctx *h, const void *in, void *out) {
+    BandArgsF a{};
+    a.g = h->log_unary;
+    a.in = (const float *)in;
+    a.out = (float *)out;
+    a.d = h->dims;
+    a.parity = -1;
+    a.T = h->Teff;
+    for (int i = 0; i < 2 * h->Teff + 1; ++i) a.w[i] = h->wf[i];
+    a.fbar = h->fbarf;
+    return a;
+}
+
 bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
-    (void)n_iters;
-    return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_iterate: BP_RECORD is not available in this build");
+    const int c = h->ckpt_every;
+    const int n_ck = (n_iters + c - 1) / c;
+    const size_t sb = bpg_state_bytes(h);
+    while ((int)h->ckpts.size() < n_ck) {
+        void *p = nullptr;
+        if (bp_status st = bpg_ensure_buffer(h, &p, sb, "checkpoint")) return st;
+        h->ckpts.push_back(p);
+    }
+    for (int t = 0; t < n_iters; ++t) {
+        if (t % c == 0)
+            BK_CK(h, cudaMemcpyAsync(h->ckpts[t / c], h->msg[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream));
+        BK_CK(h, launch_band_log(log_args(h, h->msg[h->cur], h->msg[h->cur ^ 1]), h->layout, h->blocks_override,
+                                 h->stream));
+        h->cur ^= 1;
+        h->launches += 1;
+    }
+    h->rec_iters = n_iters;
+    h->rec_every = c;
+    h->recorded = true;
+    return BP_OK;
 }
 
 extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
                                  double *host_dfbar) {
-    (void)dev_dlogb; (void)dev_dlogg; (void)host_dtable; (void)host_dfbar;
-    if (!h) return BP_ERR_ARG;
-    return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward is not available in this build");
+    if (!h) return bpg_fail(nullptr, BP_ERR_ARG, "bp_backward: NULL handle");
+    h->err.clear();
+    if (!dev_dlogb || !dev_dlogg || !host_dtable || !host_dfbar)
+        return bpg_fail(h, BP_ERR_ARG, "bp_backward: NULL argument");
+    if (!h->recorded || !h->msg_log)
+        return bpg_fail(h, BP_ERR_STATE, "bp_backward: run bp_iterate with BP_SUM|BP_LOG|BP_RECORD first");
+    if (!h->fast) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: needs T <= 8 and M <= 512");
+    if (bp_status st = bpg_check_device(h)) return st;
+    const int K = h->rec_iters, c = h->rec_every, Teff = h->Teff, NP = 2 * Teff + 2;
+    const size_t sb = bpg_state_bytes(h);
+    const long long nodes = (long long)h->W * h->H;
+    const int blocks = adjoint_blocks(h->dims, h->layout, Teff);
+    if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: no adjoint kernel for this layout");
+    const int seg_states = c > 1 ? c - 1 : 1;
+    if (h->seg_cap < seg_states) {
+        if (h->seg_buf) { cudaFree(h->seg_buf); h->seg_buf = nullptr; }
+        if (bp_status st = bpg_ensure_buffer(h, &h->seg_buf, sb * seg_states, "segment states")) return st;
+        h->seg_cap = seg_states;
+    }
+    if (bp_status st = bpg_ensure_buffer(h, &h->adj[0], sb, "adjoint state")) return st;
+    if (bp_status st = bpg_ensure_buffer(h, &h->adj[1], sb, "adjoint state")) return st;
+    if (bp_status st = bpg_ensure_buffer(h, &h->dlogg_pad, (size_t)nodes * h->Mp * 4, "dlogg")) return st;
+    const long long rows = (long long)K * blocks;
+    const size_t pbytes = (size_t)(rows > 0 ? rows : 1) * NP * 4;
+    if (h->dtab_cap < pbytes) {
+        if (h->dtab_partial) { cudaFree(h->dtab_partial); h->dtab_partial = nullptr; }
+        if (bp_status st = bpg_ensure_buffer(h, &h->dtab_partial, pbytes, "gradient partial sums")) return st;
+        h->dtab_cap = pbytes;
+    }
+    if (bp_status st = bpg_ensure_buffer(h, &h->d_red, (2 * kTMaxFast + 2) * sizeof(double), "gradient sums"))
+        return st;
+
+    // reverse of the beliefs: seeds the adjoint of the final messages and dL/d log g
+    BK_CK(h, launch_beliefs_log_adjoint(h->log_unary, (const float *)h->msg[h->cur], dev_dlogb, h->dims,
+                                        (float *)h->adj[0], (float *)h->dlogg_pad, h->stream));
+    h->launches += 1;
+    int ca = 0;
+    const int n_ck = (K + c - 1) / c;
+    std::vector<void *> states(c);
+    for (int seg = n_ck - 1; seg >= 0; --seg) {
+        const int start = seg * c, end = std::min(K, start + c), len = end - start;
+        states[0] = h->ckpts[seg];
+        for (int j = 1; j < len; ++j) {
+            states[j] = (char *)h->seg_buf + (size_t)(j - 1) * sb;
+            BK_CK(h, launch_band_log(log_args(h, states[j - 1], states[j]), h->layout, h->blocks_override, h->stream));
+            h->launches += 1;
+        }
+        for (int t = end - 1; t >= start; --t) {
+            AdjArgs a{};
+            a.logg = h->log_unary;
+            a.ell = (const float *)states[t - start];
+            a.lam_next = (const float *)h->adj[ca];
+            a.lam = (float *)h->adj[ca ^ 1];
+            a.dlogg = (float *)h->dlogg_pad;
+            a.partial = (float *)h->dtab_partial + (size_t)t * blocks * NP;
+            a.d = h->dims;
+            a.T = Teff;
+            for (int i = 0; i < 2 * Teff + 1; ++i) a.w[i] = h->wf[i];
+            a.fbar = h->fbarf;
+            BK_CK(h, launch_band_log_adjoint(a, h->layout, blocks, h->stream));
+            h->launches += 1;
+            ca ^= 1;
+        }
+    }
+    std::vector<double> red(NP, 0.0);
+    if (rows > 0) {
+        BK_CK(h, launch_reduce_partials_f64((const float *)h->dtab_partial, rows, NP, (double *)h->d_red, h->stream));
+        h->launches += 1;
+        BK_CK(h, cudaMemcpyAsync(red.data(), h->d_red, NP * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    BK_CK(h, launch_unpad_copy(h->dlogg_pad, dev_dlogg, nodes, h->M, h->Mp, h->stream));
+    h->launches += 1;
+    if (bp_status st = bp_sync(h)) return st;
+    for (int d = -h->T; d <= h->T; ++d) host_dtable[d + h->T] = (d >= -Teff && d <= Teff) ? red[d + Teff] : 0.0;
+    *host_dfbar = red[NP - 1];
+    return BP_OK;
 }

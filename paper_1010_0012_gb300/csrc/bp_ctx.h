@@ -71,8 +71,11 @@ struct bp_ctx {
     void *seg_buf = nullptr;        // recomputed states of one segment
     int seg_cap = 0;
     void *adj[2] = {nullptr, nullptr};   // adjoint message states
-    void *dtab_partial = nullptr;   // per-block partial sums of d table, d fbar
-    int dtab_blocks = 0;
+    void *dtab_partial = nullptr;   // per-(iteration, block) partial sums of d table, d fbar
+    size_t dtab_cap = 0;
+    void *dlogg_pad = nullptr;      // [H][W][Mp] accumulated dL/d log g
+    void *d_red = nullptr;          // FP64 reduced parameter gradients
+    int rec_every = 5;
 
     // tensor-core dense baseline
     void *tc_a = nullptr;           // packed h rows, bf16 [4*H*W][Mp]

@@ -107,8 +107,9 @@ cudaError_t launch_dense_sum(const DenseArgsF &a, cudaStream_t s);
 cudaError_t launch_dense_min(const DenseArgsI &a, cudaStream_t s);
 
 // Utility kernels (aux_kernels.cu).
+// transform: 0 copy, 1 log, 2 exp
 cudaError_t launch_pad_copy_f32(const float *src, float *dst, long long nodes, int M, int Mp,
-                                int log_transform, cudaStream_t s);
+                                int transform, cudaStream_t s);
 cudaError_t launch_pad_copy_i32(const int32_t *src, int32_t *dst, long long nodes, int M, int Mp,
                                 cudaStream_t s);
 cudaError_t launch_unpad_copy(const void *src, void *dst, long long rows, int M, int Mp,

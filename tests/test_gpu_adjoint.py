@@ -1,0 +1,115 @@
+"""Log-domain forward and the adjoint kernel against the FP64 oracle.
+
+Forward: log-beliefs within 1e-5 relative (per node, as for the linear path).
+Gradient: elementwise dL/d log g, dL/df(d), dL/dfbar against torch autograd of
+the FP64 dense forward, and dL/d alpha, fbar, beta against central finite
+differences in FP64, within 1e-4 * max(1, |reference|)."""
+import numpy as np
+import pytest
+
+from oracle import gradient, grid
+from paper_1010_0012_gb300 import workload as wl
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+GRAD_TOL = 1e-4
+
+
+def _close(got, ref, tol=GRAD_TOL):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.all(np.abs(got - ref) <= tol * np.maximum(1.0, np.abs(ref)))
+
+
+@pytest.mark.parametrize("M,T,schedule", [(16, 2, "sync"), (17, 1, "sync"), (64, 3, "sync"), (32, 4, "redblack")])
+def test_log_forward_matches_oracle(M, T, schedule):
+    cfg = wl.small_config("lg", 19, 11, M, T, alpha=0.9, structure="planar", seed=M)
+    st, g, _ = H.stereo_inputs(cfg)
+    tab, fbar = wl.pair_table_f32(cfg.alpha, T)
+    H.check_sum_case(g, tab, T, fbar, 7, schedule, log=True)
+
+
+def _gpu_grad(cost, d_gt, alpha, fbar, beta, T, K, every):
+    import torch
+    from paper_1010_0012_gb300 import autograd, bp
+    Hh, W, M = cost.shape
+    G = bp.BPGrid(W, Hh, M, bp.BP_F32)
+    a = torch.tensor(alpha, dtype=torch.float32, requires_grad=True)
+    fb = torch.tensor(fbar, dtype=torch.float32, requires_grad=True)
+    b = torch.tensor(beta, dtype=torch.float32, device="cuda", requires_grad=True)
+    cost_t = torch.from_numpy(np.ascontiguousarray(cost, dtype=np.float32)).cuda()
+    loss = autograd.stereo_nll(cost_t, d_gt, a, fb, b, T, K, G, every)
+    loss.backward()
+    out = {"loss": float(loss), "d_alpha": float(a.grad), "d_fbar": float(fb.grad), "d_beta": float(b.grad)}
+    G.close()
+    return out
+
+
+def test_adjoint_elementwise_against_fp64_autograd():
+    import torch
+    from paper_1010_0012_gb300 import autograd, bp
+    cfg = wl.small_config("ad", 12, 9, 16, 2, alpha=1.0, structure="planar", seed=5)
+    st = wl.make_stereo(cfg)
+    T, K, beta = cfg.T, 6, 0.1
+    d = np.arange(-T, T + 1)
+    table = np.exp(-cfg.alpha * np.abs(d)).astype(np.float32)
+    fbar = float(np.float32(np.exp(-cfg.alpha * T)))
+    logg = (-beta * st.cost.astype(np.float64)).astype(np.float32)
+    ref = gradient.reference_gradient_table(-logg.astype(np.float64) / beta, st.d_gt, table.astype(np.float64),
+                                            fbar, beta, T, K)
+    G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_F32)
+    lg = torch.from_numpy(logg).cuda().requires_grad_(True)
+    tab = torch.from_numpy(table).requires_grad_(True)
+    fb = torch.tensor(fbar, dtype=torch.float32, requires_grad=True)
+    logb = autograd.log_beliefs(lg, tab, fb, G, T, K, every=2)
+    idx = torch.as_tensor(st.d_gt, dtype=torch.long, device="cuda")[..., None]
+    loss = -torch.gather(logb, -1, idx).sum()
+    loss.backward()
+    assert abs(float(loss) - ref["loss"]) <= 1e-5 * abs(ref["loss"])
+    assert _close(lg.grad.cpu().numpy(), ref["d_logg"])
+    assert _close(tab.grad.numpy(), ref["d_table"])
+    assert _close(float(fb.grad), ref["d_fbar"])
+    G.close()
+
+
+@pytest.mark.parametrize("every", [1, 4, 13])
+def test_checkpoint_interval_does_not_change_the_gradient(every):
+    cfg = wl.small_config("ck", 14, 10, 32, 3, alpha=0.7, structure="planar", seed=9)
+    st = wl.make_stereo(cfg)
+    base = _gpu_grad(st.cost, st.d_gt, 0.7, float(np.exp(-0.7 * 3)), 0.1, 3, 13, 13)
+    got = _gpu_grad(st.cost, st.d_gt, 0.7, float(np.exp(-0.7 * 3)), 0.1, 3, 13, every)
+    for k in base:
+        assert got[k] == base[k], (k, got[k], base[k])
+
+
+@pytest.mark.parametrize("W,Hh,K", [(40, 32, 30), (256, 256, 30)])
+def test_parameter_gradients_against_finite_differences(W, Hh, K):
+    """The 256 x 256, M = 64, T = 3, 30-iteration workload (checkpoint every 5)
+    and a reduced grid with the same recipe."""
+    base = wl.CONFIGS["grid256_m64_grad"]
+    import dataclasses
+    cfg = dataclasses.replace(base, W=W, H=Hh)
+    st = wl.make_stereo(cfg)
+    alpha, beta, T = cfg.alpha, cfg.beta, cfg.T
+    fbar = float(np.exp(-alpha * T))
+    # both sides see the same float32-rounded parameters
+    alpha32, fbar32, beta32 = (float(np.float32(v)) for v in (alpha, fbar, beta))
+    gpu = _gpu_grad(st.cost, st.d_gt, alpha32, fbar32, beta32, T, K, 5)
+    fd = gradient.finite_difference(st.cost.astype(np.float64), st.d_gt, alpha32, fbar32, beta32, T, K)
+    for k in ("d_alpha", "d_fbar", "d_beta"):
+        assert _close(gpu[k], fd[k]), (k, gpu[k], fd[k])
+
+
+def test_backward_without_recorded_forward_is_a_state_error():
+    import torch
+    from paper_1010_0012_gb300 import bp
+    G = bp.BPGrid(6, 5, 16, bp.BP_F32)
+    G.set_unary(torch.ones((5, 6, 16), device="cuda"))
+    tab, fbar = wl.pair_table_f32(1.0, 2)
+    G.set_potential(tab, 2, fbar)
+    G.reset()
+    G.iterate(3, bp.BP_SUM | bp.BP_LOG)
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_backward(G.h, torch.zeros((5, 6, 16), device="cuda"), torch.zeros((5, 6, 16), device="cuda"), 5)
+    assert ei.value.status == bp.BP_ERR_STATE
+    G.close()

@@ -60,3 +60,21 @@ def test_dlogg_matches_finite_difference_on_one_entry():
             return float(gradient.nll_loss(logg, alpha, fbar, T, 5, st.d_gt))
     fd = (loss_at(h) - loss_at(-h)) / (2 * h)
     assert abs(ref["d_logg"][r, c, x] - fd) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_table_parameterisation_chain_rule_matches_alpha_gradient():
+    """d/d alpha through f(d) = exp(-alpha |d|) (chain rule on d/d f(d)) equals
+    the direct d/d alpha; d/d fbar and d/d log g agree between the two forms."""
+    st = _small(W=6, H=5, M=7, T=2, seed=21)
+    alpha, beta, T = 0.8, 0.1, 2
+    fbar = float(np.exp(-alpha * T))
+    cost = st.cost.astype(np.float64)
+    d = np.arange(-T, T + 1)
+    table = np.exp(-alpha * np.abs(d))
+    a = gradient.reference_gradient(cost, st.d_gt, alpha, fbar, beta, T, 5)
+    b = gradient.reference_gradient_table(cost, st.d_gt, table, fbar, beta, T, 5)
+    assert abs(a["loss"] - b["loss"]) <= 1e-12 * abs(a["loss"])
+    chain = float(np.sum(b["d_table"] * -np.abs(d) * table))
+    assert abs(chain - a["d_alpha"]) <= 1e-10 * max(1.0, abs(a["d_alpha"]))
+    assert abs(b["d_fbar"] - a["d_fbar"]) <= 1e-10 * max(1.0, abs(a["d_fbar"]))
+    np.testing.assert_allclose(b["d_logg"], a["d_logg"], rtol=1e-10, atol=1e-13)
