@@ -60,7 +60,9 @@ def stereo_nll(cost, d_gt, alpha, fbar, beta, T, n_iters, grid, every=5):
     for |d| <= T and fbar outside.  Autograd's chain rule maps the library's
     dL/d log g, dL/df(d), dL/dfbar to dL/d beta, d alpha, d fbar."""
     dev = cost.device
-    logg = -beta.to(dev) * cost
+    # the chain rule to beta sums dL/d log g * cost over every node: keep that
+    # reduction in FP64 (the library's log g stays FP32)
+    logg = (-beta.to(dev).double() * cost.double()).float()
     d = torch.arange(-T, T + 1, dtype=torch.float32, device=alpha.device).abs()
     table = torch.exp(-alpha * d)
     logb = log_beliefs(logg.float().contiguous(), table, fbar, grid, T, n_iters, every)
