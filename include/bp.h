@@ -179,6 +179,52 @@ bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const float *dev_unar
                                       float *dev_out_planes, const float *host_table, int T, double fbar,
                                       void *cuda_stream);
 
+/* ---- batches of independent MRFs --------------------------------------------
+ * Many MRFs of different size, label count and band width (each an H x W
+ * grid as above, homogeneous within itself; Eq. 1 with per-MRF potentials,
+ * the inhomogeneous case of Sec. 1) advanced together by ONE persistent
+ * cooperative kernel launch per bp_batch_iterate call, captured once in a CUDA
+ * graph and replayed.  Synchronous schedule only; 2 <= M <= 256, band
+ * half-width min(T, M-1) <= 8. */
+typedef struct {
+    int W, H, M;               /* grid and label count of this MRF                 */
+    int T;                     /* band half-width                                  */
+    const void *dev_unary;     /* [H][W][M] g (float32) or E_u (int32); copied     */
+    const void *host_table;    /* 2T+1 values f(d) (float32) or E(d) (int32)       */
+    double fbar;               /* fbar, or the integer Ebar for min-sum            */
+} bp_mrf_desc;
+
+typedef struct bp_batch_ctx *bp_batch;
+
+/* Validate the n descriptors (as bp_set_potential would: BP_ERR_POTENTIAL for
+ * E(d) > Ebar), allocate every MRF's unary and two message states, copy the
+ * unaries, and cut the nodes into work items.  cuda_stream as in bp_create. */
+bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void *cuda_stream, bp_batch *out);
+bp_status bp_batch_reset_messages(bp_batch b);
+/* n_iters synchronous iterations of every MRF in one launch.  mode BP_SUM
+ * (float32 batch) or BP_MAX (int32 batch).  Between iterations the blocks meet
+ * at a grid barrier whose wait is bounded; a wait that runs out ends the
+ * kernel and the next bp_batch_sync returns BP_ERR_TIMEOUT. */
+bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode);
+/* Beliefs / MAP (as bp_beliefs) and message planes (as bp_get_messages) of MRF k. */
+bp_status bp_batch_beliefs(bp_batch b, int k, void *dev_out, int32_t *dev_map);
+bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes);
+/* Work decomposition: family 1 (4 labels per lane, C = 1) or 2 (8 labels per
+ * lane) and the item size in label words.  bp_batch_autotune times every
+ * candidate on this batch, keeps the fastest (cached in $BP_AUTOTUNE_CACHE when
+ * set) and resets the messages. */
+bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words);
+bp_status bp_batch_get_tiling(bp_batch b, int *family, int *tile_words);
+bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms);
+/* Bound of the grid-barrier wait (default 2 s).  extra_arrivals = 1 makes the
+ * barrier wait for one block that does not exist, so that every wait runs
+ * out: a fault-free way to exercise the time-out path. */
+bp_status bp_batch_set_wait_limit(bp_batch b, double seconds, int extra_arrivals);
+bp_status bp_batch_sync(bp_batch b);
+const char *bp_batch_last_error(bp_batch b);
+long long bp_batch_launch_count(bp_batch b);
+void bp_batch_destroy(bp_batch b);
+
 /* Number of kernel launches the library issued on this handle so far. */
 long long bp_launch_count(bp_handle h);
 

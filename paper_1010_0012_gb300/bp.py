@@ -60,6 +60,19 @@ def _load():
         "bp_launch_count": ([P], ctypes.c_longlong),
         "bp_iterate_dense_tc_noalloc": ([I, I, I, P, P, P, P, I, D, P], I),
         "bp_version": ([], I),
+        "bp_batch_create": ([I, P, I, P, ctypes.POINTER(P)], I),
+        "bp_batch_reset_messages": ([P], I),
+        "bp_batch_iterate": ([P, I, I], I),
+        "bp_batch_beliefs": ([P, I, P, P], I),
+        "bp_batch_get_messages": ([P, I, P], I),
+        "bp_batch_set_tiling": ([P, I, I], I),
+        "bp_batch_get_tiling": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bp_batch_autotune": ([P, I, I, ctypes.POINTER(ctypes.c_float)], I),
+        "bp_batch_set_wait_limit": ([P, D, I], I),
+        "bp_batch_sync": ([P], I),
+        "bp_batch_last_error": ([P], ctypes.c_char_p),
+        "bp_batch_launch_count": ([P], ctypes.c_longlong),
+        "bp_batch_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -208,6 +221,90 @@ def bp_iterate_dense_tc_noalloc(W, H, M, unary: torch.Tensor, in_planes: torch.T
                                           tab.ctypes.data_as(ctypes.c_void_p), int(T), float(fbar),
                                           _stream_ptr(stream))
     _check(None, st)
+
+
+# ---- batches ---------------------------------------------------------------------
+
+class bp_mrf_desc(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("M", ctypes.c_int), ("T", ctypes.c_int),
+                ("dev_unary", ctypes.c_void_p), ("host_table", ctypes.c_void_p), ("fbar", ctypes.c_double)]
+
+
+def _bcheck(b, st):
+    if st != BP_OK:
+        raise BPError(st, _lib.bp_batch_last_error(b).decode())
+
+
+def bp_batch_create(mrfs, dtype, stream=None):
+    """mrfs: list of (unary tensor [H][W][M], table, T, fbar)."""
+    import numpy as np
+    descs = (bp_mrf_desc * len(mrfs))()
+    keep = []
+    for i, (un, table, T, fbar) in enumerate(mrfs):
+        Hh, W, M = un.shape
+        tab = np.ascontiguousarray(table, dtype=np.float32 if dtype == BP_F32 else np.int32)
+        if tab.size != 2 * T + 1:
+            raise ValueError("table must hold 2T + 1 values")
+        keep.append(tab)
+        descs[i] = bp_mrf_desc(W, Hh, M, T, _dptr(un, torch.float32 if dtype == BP_F32 else torch.int32).value,
+                               tab.ctypes.data, float(fbar))
+    b = ctypes.c_void_p()
+    st = _lib.bp_batch_create(len(mrfs), descs, dtype, _stream_ptr(stream), ctypes.byref(b))
+    _bcheck(None, st)
+    return b
+
+
+def bp_batch_reset_messages(b):
+    _bcheck(b, _lib.bp_batch_reset_messages(b))
+
+
+def bp_batch_iterate(b, n_iters, mode):
+    _bcheck(b, _lib.bp_batch_iterate(b, int(n_iters), int(mode)))
+
+
+def bp_batch_beliefs(b, k, out: torch.Tensor, map_out: Optional[torch.Tensor] = None):
+    mp = None if map_out is None else _dptr(map_out, torch.int32)
+    _bcheck(b, _lib.bp_batch_beliefs(b, int(k), ctypes.c_void_p(out.data_ptr()), mp))
+
+
+def bp_batch_get_messages(b, k, planes: torch.Tensor):
+    _bcheck(b, _lib.bp_batch_get_messages(b, int(k), ctypes.c_void_p(planes.data_ptr())))
+
+
+def bp_batch_set_tiling(b, family, tile_words):
+    _bcheck(b, _lib.bp_batch_set_tiling(b, int(family), int(tile_words)))
+
+
+def bp_batch_get_tiling(b):
+    f, t = ctypes.c_int(), ctypes.c_int()
+    _bcheck(b, _lib.bp_batch_get_tiling(b, ctypes.byref(f), ctypes.byref(t)))
+    return f.value, t.value
+
+
+def bp_batch_autotune(b, mode, n_iters=3):
+    ms = ctypes.c_float(0.0)
+    _bcheck(b, _lib.bp_batch_autotune(b, int(mode), int(n_iters), ctypes.byref(ms)))
+    return ms.value
+
+
+def bp_batch_set_wait_limit(b, seconds, extra_arrivals=0):
+    _bcheck(b, _lib.bp_batch_set_wait_limit(b, float(seconds), int(extra_arrivals)))
+
+
+def bp_batch_sync(b):
+    _bcheck(b, _lib.bp_batch_sync(b))
+
+
+def bp_batch_last_error(b=None):
+    return _lib.bp_batch_last_error(b).decode()
+
+
+def bp_batch_launch_count(b):
+    return _lib.bp_batch_launch_count(b)
+
+
+def bp_batch_destroy(b):
+    _lib.bp_batch_destroy(b)
 
 
 # ---- a thin owner of one handle -------------------------------------------------

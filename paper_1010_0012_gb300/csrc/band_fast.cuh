@@ -149,51 +149,78 @@ __device__ __forceinline__ long long out_offset(int t, int r, int c, int W, long
     return dst_plane * plane + ((long long)(r + dr) * W + (c + dc)) * Mp;
 }
 
+// Message loads: read-only ("nc") when the messages were written by an earlier
+// launch; coherent at L2 ("cg") inside a persistent launch whose other blocks
+// wrote them.
+template <bool COH, int V>
+__device__ __forceinline__ void ld_msg(float (&v)[V], const float *p) {
+    if (COH) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+            const float4 t = __ldcg(reinterpret_cast<const float4 *>(p) + i);
+            v[4 * i + 0] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else {
+        ld_vec<V>(v, p);
+    }
+}
+template <bool COH, int V>
+__device__ __forceinline__ void ld_msg(int32_t (&v)[V], const int32_t *p) {
+    if (COH) {
+#pragma unroll
+        for (int i = 0; i < V / 4; ++i) {
+            const int4 t = __ldcg(reinterpret_cast<const int4 *>(p) + i);
+            v[4 * i + 0] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    } else {
+        ld_vec<V>(v, p);
+    }
+}
+
 // ----------------------------------------------- sum-product (linear/log) ----
+// One lane's share of the update of one node: the constants of the band
+// (weights, normaliser weights) are set once per grid, node() runs per node.
 // LOG = false: linear messages, g is the unary.  LOG = true: log-messages,
 // g holds log g; h is formed as exp(log h - max log h), which leaves the
 // normalised result unchanged.
-template <int L, int C, int T, bool LOG>
-__global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
-    constexpr int V = 4 * C;
-    constexpr int GPB = kBlock / L;
-    const int q = threadIdx.x & (L - 1);
-    const int grp = threadIdx.x / L;
-    const int W = a.d.W, H = a.d.H, M = a.d.M, Mp = a.d.Mp;
-    const long long plane = a.d.plane;
-
+template <int L, int C, int T, bool LOG, bool COH>
+struct SumBand {
+    static constexpr int V = 4 * C;
     float w[2 * T + 1];
-#pragma unroll
-    for (int i = 0; i < 2 * T + 1; ++i) w[i] = a.w[i];
-    const float fbar = a.fbar;
-
-    // per-label normaliser weights c(x) + M fbar (0 on padded labels)
+    float fbar;
     float cz[V];
     bool lab_ok[V];
+    int q;
+
+    __device__ __forceinline__ void setup(const float *wsrc, float fb, int M, int lane_q) {
+        q = lane_q;
+        fbar = fb;
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const int x = q * V + k;
-        float cx = 0.f;
+        for (int i = 0; i < 2 * T + 1; ++i) w[i] = wsrc[i];
+        // per-label normaliser weights c(x) + M fbar (0 on padded labels)
 #pragma unroll
-        for (int d = -T; d <= T; ++d)
-            if (x - d >= 0 && x - d < M) cx += w[d + T];
-        lab_ok[k] = x < M;
-        cz[k] = lab_ok[k] ? cx + (float)M * fbar : 0.f;
+        for (int k = 0; k < V; ++k) {
+            const int x = q * V + k;
+            float cx = 0.f;
+#pragma unroll
+            for (int d = -T; d <= T; ++d)
+                if (x - d >= 0 && x - d < M) cx += w[d + T];
+            lab_ok[k] = x < M;
+            cz[k] = lab_ok[k] ? cx + (float)M * fbar : 0.f;
+        }
     }
 
-    const int nslots = num_slots(W, H, a.parity);
-    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
-        int r, c;
-        const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
+    __device__ __forceinline__ void node(const float *g, const float *in, float *out, int W, int H, int Mp,
+                                         long long plane, int r, int c, bool valid) const {
         const long long off = ((long long)r * W + c) * Mp + q * V;
         const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
         const float absent = LOG ? 0.f : 1.f;
 
         float gv[V], m[4][V];
-        if (valid) ld_vec<V>(gv, a.g + off); else fill_vec<V>(gv, LOG ? 0.f : 0.f);
+        if (valid) ld_vec<V>(gv, g + off); else fill_vec<V>(gv, 0.f);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            if (has[s]) ld_vec<V>(m[s], a.in + s * plane + off);
+            if (has[s]) ld_msg<COH, V>(m[s], in + s * plane + off);
             else fill_vec<V>(m[s], absent);
         }
 
@@ -246,41 +273,54 @@ __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
                 const float mv = fmaf(acc, inv, base_term);
                 o[k] = lab_ok[k] ? (LOG ? logf(mv) : mv) : 0.f;
             }
-            if (has[t]) st_vec<V>(a.out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
+            if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
         }
+    }
+};
+
+template <int L, int C, int T, bool LOG>
+__global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
+    constexpr int GPB = kBlock / L;
+    const int grp = threadIdx.x / L;
+    SumBand<L, C, T, LOG, false> band;
+    band.setup(a.w, a.fbar, a.d.M, threadIdx.x & (L - 1));
+    const int W = a.d.W;
+    const int nslots = num_slots(W, a.d.H, a.parity);
+    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
+        int r, c;
+        const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
+        band.node(a.g, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid);
     }
 }
 
 // ------------------------------------------------------------- min-sum ------
-template <int L, int C, int T>
-__global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
-    constexpr int V = 4 * C;
-    constexpr int GPB = kBlock / L;
-    const int q = threadIdx.x & (L - 1);
-    const int grp = threadIdx.x / L;
-    const int W = a.d.W, H = a.d.H, M = a.d.M, Mp = a.d.Mp;
-    const long long plane = a.d.plane;
-
+template <int L, int C, int T, bool COH>
+struct MinBand {
+    static constexpr int V = 4 * C;
     int32_t w[2 * T + 1];
-#pragma unroll
-    for (int i = 0; i < 2 * T + 1; ++i) w[i] = a.w[i];
-    const int32_t ebar = a.ebar;
+    int32_t ebar;
     bool lab_ok[V];
-#pragma unroll
-    for (int k = 0; k < V; ++k) lab_ok[k] = q * V + k < M;
+    int q;
 
-    const int nslots = num_slots(W, H, a.parity);
-    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
-        int r, c;
-        const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
+    __device__ __forceinline__ void setup(const int32_t *wsrc, int32_t eb, int M, int lane_q) {
+        q = lane_q;
+        ebar = eb;
+#pragma unroll
+        for (int i = 0; i < 2 * T + 1; ++i) w[i] = wsrc[i];
+#pragma unroll
+        for (int k = 0; k < V; ++k) lab_ok[k] = q * V + k < M;
+    }
+
+    __device__ __forceinline__ void node(const int32_t *e, const int32_t *in, int32_t *out, int W, int H, int Mp,
+                                         long long plane, int r, int c, bool valid) const {
         const long long off = ((long long)r * W + c) * Mp + q * V;
         const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
 
         int32_t ev[V], m[4][V];
-        if (valid) ld_vec<V>(ev, a.e + off); else fill_vec<V, int32_t>(ev, 0);
+        if (valid) ld_vec<V>(ev, e + off); else fill_vec<V, int32_t>(ev, 0);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            if (has[s]) ld_vec<V>(m[s], a.in + s * plane + off);
+            if (has[s]) ld_msg<COH, V>(m[s], in + s * plane + off);
             else fill_vec<V, int32_t>(m[s], 0);
         }
 
@@ -315,8 +355,23 @@ __global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
             umin = group_min<L>(umin);
 #pragma unroll
             for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
-            if (has[t]) st_vec<V>(a.out + out_offset(t, r, c, W, plane, Mp) + q * V, u);
+            if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, u);
         }
+    }
+};
+
+template <int L, int C, int T>
+__global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
+    constexpr int GPB = kBlock / L;
+    const int grp = threadIdx.x / L;
+    MinBand<L, C, T, false> band;
+    band.setup(a.w, a.ebar, a.d.M, threadIdx.x & (L - 1));
+    const int W = a.d.W;
+    const int nslots = num_slots(W, a.d.H, a.parity);
+    for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
+        int r, c;
+        const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
+        band.node(a.e, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid);
     }
 }
 

@@ -1,0 +1,148 @@
+// Persistent O(mM) kernel for a batch of independent MRFs of uneven size,
+// label count and band width.
+//
+// One cooperative launch runs every iteration of every MRF.  The nodes of all
+// MRFs are cut into work items (mrf, first node, node count) of roughly equal
+// bytes; block b takes items b, b + G, b + 2G, ... and, per item, runs the
+// per-node update (SumBand / MinBand) compiled for that MRF's padded label
+// count and band half-width.  Between iterations all blocks meet at a grid
+// barrier whose wait is bounded: on time-out the block records an error code
+// in the status word and the kernel returns (the host reports BP_ERR_TIMEOUT).
+// Messages written by other blocks are read with L2-coherent loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "band_fast.cuh"
+#include "bp_batch_internal.h"
+
+namespace bpg {
+
+__device__ __forceinline__ unsigned long long batch_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Sense-reversing grid barrier over `expected` arrivals.  Returns false (in
+// every thread of the block) if the wait ran out.
+__device__ __forceinline__ bool batch_grid_barrier(unsigned *count, unsigned *gen, unsigned expected,
+                                                   unsigned long long limit_ns, int *status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        if (arrived == expected) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const unsigned long long t0 = batch_timer();
+            while (*vgen == g) {
+                if (batch_timer() - t0 > limit_ns) {
+                    ok = 0;
+                    atomicExch(status, 201);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int L, int C, int T, bool MIN>
+__device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int node0, int count, int src) {
+    constexpr int GPB = kBlock / L;
+    const int grp = threadIdx.x / L;
+    const int q = threadIdx.x & (L - 1);
+    const int W = m->W, H = m->H, Mp = m->Mp;
+    const long long plane = m->plane;
+    const void *un = m->unary;
+    const void *in = m->msg[src];
+    void *out = m->msg[src ^ 1];
+    if (MIN) {
+        MinBand<L, C, T, true> b;
+        b.setup(m->wi, m->ebar, m->M, q);
+        for (int base = 0; base < count; base += GPB) {
+            const int n = node0 + base + grp;
+            const bool valid = base + grp < count;
+            const int r = valid ? n / W : 0;
+            const int c = valid ? n - r * W : 0;
+            b.node((const int32_t *)un, (const int32_t *)in, (int32_t *)out, W, H, Mp, plane, r, c, valid);
+        }
+    } else {
+        SumBand<L, C, T, false, true> b;
+        b.setup(m->wf, m->fbar, m->M, q);
+        for (int base = 0; base < count; base += GPB) {
+            const int n = node0 + base + grp;
+            const bool valid = base + grp < count;
+            const int r = valid ? n / W : 0;
+            const int c = valid ? n - r * W : 0;
+            b.node((const float *)un, (const float *)in, (float *)out, W, H, Mp, plane, r, c, valid);
+        }
+    }
+}
+
+template <int L, int C, bool MIN>
+__device__ __forceinline__ void batch_item_t(const BatchMrf *__restrict__ m, int node0, int count, int src) {
+    switch (m->T) {
+        case 0: batch_item<L, C, 0, MIN>(m, node0, count, src); break;
+        case 1: batch_item<L, C, 1, MIN>(m, node0, count, src); break;
+        case 2: batch_item<L, C, 2, MIN>(m, node0, count, src); break;
+        case 3: batch_item<L, C, 3, MIN>(m, node0, count, src); break;
+        case 4: batch_item<L, C, 4, MIN>(m, node0, count, src); break;
+        case 5: batch_item<L, C, 5, MIN>(m, node0, count, src); break;
+        case 6: batch_item<L, C, 6, MIN>(m, node0, count, src); break;
+        case 7: batch_item<L, C, 7, MIN>(m, node0, count, src); break;
+        default: batch_item<L, C, 8, MIN>(m, node0, count, src); break;
+    }
+}
+
+// Family 1: the fewest labels per lane (C = 1 up to 128 labels);
+// family 2: two 4-label chunks per lane.  Padded label counts 16..256.
+template <int FAM, bool MIN>
+__device__ __forceinline__ void batch_dispatch(const BatchMrf *__restrict__ m, int node0, int count, int src) {
+    if (FAM == 1) {
+        switch (m->Mp) {
+            case 16: batch_item_t<4, 1, MIN>(m, node0, count, src); break;
+            case 32: batch_item_t<8, 1, MIN>(m, node0, count, src); break;
+            case 64: batch_item_t<16, 1, MIN>(m, node0, count, src); break;
+            case 128: batch_item_t<32, 1, MIN>(m, node0, count, src); break;
+            default: batch_item_t<32, 2, MIN>(m, node0, count, src); break;
+        }
+    } else {
+        switch (m->Mp) {
+            case 16: batch_item_t<2, 2, MIN>(m, node0, count, src); break;
+            case 32: batch_item_t<4, 2, MIN>(m, node0, count, src); break;
+            case 64: batch_item_t<8, 2, MIN>(m, node0, count, src); break;
+            case 128: batch_item_t<16, 2, MIN>(m, node0, count, src); break;
+            default: batch_item_t<32, 2, MIN>(m, node0, count, src); break;
+        }
+    }
+}
+
+template <int FAM, bool MIN>
+__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
+    for (int t = 0; t < a.n_iters; ++t) {
+        const int src = (a.start_buf + t) & 1;
+        for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+            const BatchItem item = a.items[it];
+            batch_dispatch<FAM, MIN>(a.mrfs + item.mrf, item.node0, item.count, src);
+        }
+        if (t + 1 < a.n_iters) {
+            __threadfence();
+            if (!batch_grid_barrier(a.bar_count, a.bar_gen, gridDim.x + a.extra_arrivals, a.limit_ns, a.status))
+                return;
+        }
+    }
+}
+
+}  // namespace bpg

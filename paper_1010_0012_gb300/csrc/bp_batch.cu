@@ -1,0 +1,488 @@
+// Batched O(mM) belief propagation: many independent MRFs of uneven size,
+// label count and band width advanced by one persistent cooperative launch
+// per bp_batch_iterate call (captured once in a CUDA graph and replayed).
+// Declarations and the contract of every call are in include/bp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bp.h"
+#include "bp_batch_internal.h"
+#include "bp_ctx.h"
+
+using namespace bpg;
+
+namespace bpg {
+cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
+cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
+int batch_max_blocks_sum(int family);
+int batch_max_blocks_min(int family);
+
+int batch_lanes_per_node(int family, int Mp) {
+    if (family == 1) return Mp >= 256 ? 32 : Mp / 4;
+    return Mp >= 256 ? 32 : Mp / 8;
+}
+}  // namespace bpg
+
+namespace {
+
+struct MrfHost {
+    int W, H, M, Mp, T, Teff;
+    std::vector<float> tablef;
+    std::vector<int32_t> tablei;
+    double fbar;
+    void *unary = nullptr;
+    void *msg[2] = {nullptr, nullptr};
+};
+
+struct BatchGraphKey {
+    int n, mode, cur, family, tile, blocks;
+    bool operator<(const BatchGraphKey &o) const {
+        return std::tie(n, mode, cur, family, tile, blocks) < std::tie(o.n, o.mode, o.cur, o.family, o.tile, o.blocks);
+    }
+};
+
+thread_local std::string g_batch_err;
+
+}  // namespace
+
+struct bp_batch_ctx {
+    int n = 0;
+    bp_dtype dtype = BP_F32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<MrfHost> mrfs;
+    BatchMrf *d_mrfs = nullptr;
+    BatchItem *d_items = nullptr;
+    int n_items = 0, items_cap = 0;
+    unsigned *d_bar = nullptr;   // [count, generation]
+    int *d_status = nullptr;
+    int family = 1;
+    int tile_words = 16384;
+    int items_family = 0, items_tile = 0;
+    int cur = 0;
+    bool uniform_pending = true;
+    bool use_graphs = true;
+    std::map<BatchGraphKey, cudaGraphExec_t> graphs;
+    int extra_arrivals = 0;
+    unsigned long long limit_ns = 2000000000ull;
+    long long launches = 0;
+    std::string err;
+};
+
+static bp_status bfail(bp_batch b, bp_status st, const std::string &m) {
+    if (b) b->err = m; else g_batch_err = m;
+    return st;
+}
+
+#define BB_CK(b, call)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? BP_ERR_OOM : BP_ERR_CUDA,              \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    } while (0)
+
+static void clear_batch_graphs(bp_batch b) {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Cut every MRF into items of about `tile_words` label words, whole groups of nodes.
+static bp_status build_items(bp_batch b) {
+    std::vector<BatchItem> items;
+    for (int k = 0; k < b->n; ++k) {
+        const MrfHost &m = b->mrfs[k];
+        const int gpb = kBlock / batch_lanes_per_node(b->family, m.Mp);
+        int tile = std::max(gpb, (b->tile_words / m.Mp) / gpb * gpb);
+        const int N = m.W * m.H;
+        for (int n0 = 0; n0 < N; n0 += tile) items.push_back(BatchItem{k, n0, std::min(tile, N - n0)});
+    }
+    if ((int)items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        BB_CK(b, cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
+        b->items_cap = (int)items.size();
+    }
+    BB_CK(b, cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                             b->stream));
+    BB_CK(b, cudaStreamSynchronize(b->stream));
+    b->n_items = (int)items.size();
+    b->items_family = b->family;
+    b->items_tile = b->tile_words;
+    return BP_OK;
+}
+
+static int batch_blocks(bp_batch b) {
+    const int maxb = b->dtype == BP_I32 ? batch_max_blocks_min(b->family) : batch_max_blocks_sum(b->family);
+    return std::max(1, std::min(maxb, b->n_items));
+}
+
+static cudaError_t issue_batch(bp_batch b, int n_iters, int cur) {
+    BatchArgs a{};
+    a.mrfs = b->d_mrfs;
+    a.items = b->d_items;
+    a.n_items = b->n_items;
+    a.n_iters = n_iters;
+    a.start_buf = cur;
+    a.bar_count = b->d_bar;
+    a.bar_gen = b->d_bar + 1;
+    a.extra_arrivals = b->extra_arrivals;
+    a.limit_ns = b->limit_ns;
+    a.status = b->d_status;
+    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream);   // arrivals start at 0
+    if (e != cudaSuccess) return e;
+    const int blocks = batch_blocks(b);
+    return b->dtype == BP_I32 ? launch_batch_min(a, b->family, blocks, b->stream)
+                              : launch_batch_sum(a, b->family, blocks, b->stream);
+}
+
+static bp_status materialize_batch(bp_batch b) {
+    if (!b->uniform_pending) return BP_OK;
+    for (auto &m : b->mrfs) {
+        const long long rows = 4LL * m.W * m.H;
+        if (b->dtype == BP_I32)
+            BB_CK(b, launch_fill_messages_i32((int32_t *)m.msg[b->cur], rows, m.M, m.Mp, 0, b->stream));
+        else
+            BB_CK(b, launch_fill_messages_f32((float *)m.msg[b->cur], rows, m.M, m.Mp, 1.0f / (float)m.M, b->stream));
+        b->launches += 1;
+    }
+    b->uniform_pending = false;
+    return BP_OK;
+}
+
+extern "C" {
+
+const char *bp_batch_last_error(bp_batch b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+long long bp_batch_launch_count(bp_batch b) { return b ? b->launches : -1; }
+
+void bp_batch_destroy(bp_batch b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    clear_batch_graphs(b);
+    for (auto &m : b->mrfs) {
+        if (m.unary) cudaFree(m.unary);
+        if (m.msg[0]) cudaFree(m.msg[0]);
+        if (m.msg[1]) cudaFree(m.msg[1]);
+    }
+    void *bufs[] = {b->d_mrfs, b->d_items, b->d_bar, b->d_status};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void *cuda_stream, bp_batch *out) {
+    g_batch_err.clear();
+    if (!out) return bfail(nullptr, BP_ERR_ARG, "bp_batch_create: out is NULL");
+    *out = nullptr;
+    if (n < 1 || !descs) return bfail(nullptr, BP_ERR_ARG, "bp_batch_create: need n >= 1 descriptors");
+    if (dtype != BP_F32 && dtype != BP_I32) return bfail(nullptr, BP_ERR_ARG, "bp_batch_create: unknown dtype");
+    for (int k = 0; k < n; ++k) {
+        const bp_mrf_desc &d = descs[k];
+        std::string where = "bp_batch_create: MRF " + std::to_string(k) + ": ";
+        if (d.W < 1 || d.H < 1 || (long long)d.W * d.H > (1LL << 28))
+            return bfail(nullptr, BP_ERR_ARG, where + "bad W or H");
+        if (d.M < 2 || d.M > 256) return bfail(nullptr, BP_ERR_ARG, where + "M must be in [2, 256]");
+        if (d.T < 0 || !d.dev_unary || !d.host_table) return bfail(nullptr, BP_ERR_ARG, where + "bad T or NULL pointer");
+        if (std::min(d.T, d.M - 1) > kTMaxFast)
+            return bfail(nullptr, BP_ERR_UNSUPPORTED, where + "batched runs serve band half-widths T <= 8");
+        if (!std::isfinite(d.fbar) || d.fbar < 0) return bfail(nullptr, BP_ERR_ARG, where + "fbar must be >= 0");
+        if (dtype == BP_I32) {
+            const int32_t *t = (const int32_t *)d.host_table;
+            if (d.fbar != std::floor(d.fbar) || d.fbar >= (double)(1 << 26))
+                return bfail(nullptr, BP_ERR_ARG, where + "Ebar must be an integer in [0, 2^26)");
+            for (int i = 0; i < 2 * d.T + 1; ++i) {
+                if (t[i] < 0 || t[i] >= (1 << 26)) return bfail(nullptr, BP_ERR_ARG, where + "energies out of range");
+                if (t[i] > (int32_t)d.fbar)
+                    return bfail(nullptr, BP_ERR_POTENTIAL, where + "E(d) > Ebar; Eq. 11 needs f >= fbar (Sec. 5)");
+            }
+        } else {
+            const float *t = (const float *)d.host_table;
+            for (int i = 0; i < 2 * d.T + 1; ++i)
+                if (!std::isfinite(t[i]) || t[i] < 0) return bfail(nullptr, BP_ERR_ARG, where + "bad table entry");
+        }
+    }
+    bp_batch b = new bp_batch_ctx();
+    b->n = n;
+    b->dtype = dtype;
+    cudaGetDevice(&b->device);
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamDefault) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, BP_ERR_CUDA, "bp_batch_create: stream creation failed");
+        }
+        b->own_stream = true;
+    }
+    std::vector<BatchMrf> dm(n);
+    bp_status st = BP_OK;
+    for (int k = 0; k < n && st == BP_OK; ++k) {
+        const bp_mrf_desc &d = descs[k];
+        MrfHost m;
+        m.W = d.W; m.H = d.H; m.M = d.M; m.Mp = padded_labels(d.M);
+        if (m.Mp < 16) m.Mp = 16;
+        m.T = d.T; m.Teff = std::min(d.T, d.M - 1); m.fbar = d.fbar;
+        const size_t nodes = (size_t)d.W * d.H;
+        const size_t ub = nodes * m.Mp * 4, sb = 4 * ub;
+        b->mrfs.push_back(m);
+        MrfHost &mm = b->mrfs.back();
+        if (cudaMalloc(&mm.unary, ub) != cudaSuccess || cudaMalloc(&mm.msg[0], sb) != cudaSuccess ||
+            cudaMalloc(&mm.msg[1], sb) != cudaSuccess) {
+            cudaGetLastError();
+            st = bfail(nullptr, BP_ERR_OOM, "bp_batch_create: device allocation failed");
+            break;
+        }
+        cudaError_t e = dtype == BP_F32
+                            ? launch_pad_copy_f32((const float *)d.dev_unary, (float *)mm.unary, nodes, d.M, mm.Mp, 0, b->stream)
+                            : launch_pad_copy_i32((const int32_t *)d.dev_unary, (int32_t *)mm.unary, nodes, d.M, mm.Mp,
+                                                  b->stream);
+        if (e != cudaSuccess) { st = bfail(nullptr, BP_ERR_CUDA, "bp_batch_create: unary copy failed"); break; }
+        b->launches += 1;
+        BatchMrf &x = dm[k];
+        x = BatchMrf{};
+        x.unary = mm.unary;
+        x.msg[0] = mm.msg[0];
+        x.msg[1] = mm.msg[1];
+        x.plane = (long long)nodes * mm.Mp;
+        x.W = d.W; x.H = d.H; x.M = d.M; x.Mp = mm.Mp; x.T = mm.Teff;
+        if (dtype == BP_F32) {
+            const float *t = (const float *)d.host_table;
+            mm.tablef.assign(t, t + 2 * d.T + 1);
+            x.fbar = (float)d.fbar;
+            for (int dd = -mm.Teff; dd <= mm.Teff; ++dd) x.wf[dd + mm.Teff] = (float)((double)t[dd + d.T] - (double)x.fbar);
+        } else {
+            const int32_t *t = (const int32_t *)d.host_table;
+            mm.tablei.assign(t, t + 2 * d.T + 1);
+            x.ebar = (int32_t)d.fbar;
+            for (int dd = -mm.Teff; dd <= mm.Teff; ++dd) x.wi[dd + mm.Teff] = t[dd + d.T];
+        }
+    }
+    if (st == BP_OK) {
+        if (cudaMalloc(&b->d_mrfs, n * sizeof(BatchMrf)) != cudaSuccess ||
+            cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
+            cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            st = bfail(nullptr, BP_ERR_OOM, "bp_batch_create: device allocation failed");
+        }
+    }
+    if (st == BP_OK) {
+        if (cudaMemcpyAsync(b->d_mrfs, dm.data(), n * sizeof(BatchMrf), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+            cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream) != cudaSuccess ||
+            cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+            st = bfail(nullptr, BP_ERR_CUDA, "bp_batch_create: descriptor upload failed");
+    }
+    if (st == BP_OK) {
+        st = build_items(b);
+        if (st) g_batch_err = b->err;
+    }
+    if (st != BP_OK) {
+        bp_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return BP_OK;
+}
+
+bp_status bp_batch_reset_messages(bp_batch b) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_reset_messages: NULL batch");
+    b->err.clear();
+    b->uniform_pending = true;
+    return BP_OK;
+}
+
+bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_set_tiling: NULL batch");
+    b->err.clear();
+    if (family != 1 && family != 2) return bfail(b, BP_ERR_ARG, "bp_batch_set_tiling: family must be 1 or 2");
+    if (tile_words < 256 || tile_words > (1 << 24)) return bfail(b, BP_ERR_ARG, "bp_batch_set_tiling: tile out of range");
+    b->family = family;
+    b->tile_words = tile_words;
+    return build_items(b);
+}
+
+bp_status bp_batch_get_tiling(bp_batch b, int *family, int *tile_words) {
+    if (!b || !family || !tile_words) return bfail(b, BP_ERR_ARG, "bp_batch_get_tiling: NULL argument");
+    *family = b->family;
+    *tile_words = b->tile_words;
+    return BP_OK;
+}
+
+bp_status bp_batch_set_wait_limit(bp_batch b, double seconds, int extra_arrivals) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_set_wait_limit: NULL batch");
+    b->err.clear();
+    if (!(seconds > 0) || seconds > 60 || extra_arrivals < 0 || extra_arrivals > 1)
+        return bfail(b, BP_ERR_ARG, "bp_batch_set_wait_limit: need 0 < seconds <= 60 and extra in {0, 1}");
+    b->limit_ns = (unsigned long long)(seconds * 1e9);
+    b->extra_arrivals = extra_arrivals;
+    clear_batch_graphs(b);
+    return BP_OK;
+}
+
+bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_iterate: NULL batch");
+    b->err.clear();
+    if (n_iters < 0) return bfail(b, BP_ERR_ARG, "bp_batch_iterate: n_iters < 0");
+    if ((mode == BP_MAX) != (b->dtype == BP_I32) || (mode != BP_SUM && mode != BP_MAX))
+        return bfail(b, BP_ERR_ARG, "bp_batch_iterate: BP_SUM needs BP_F32, BP_MAX needs BP_I32");
+    if (bp_status st = materialize_batch(b)) return st;
+    if (n_iters == 0) return BP_OK;
+    if (b->items_family != b->family || b->items_tile != b->tile_words)
+        if (bp_status st = build_items(b)) return st;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BB_CK(b, cudaStreamIsCapturing(b->stream, &cap));
+    const int end_cur = (b->cur + n_iters) & 1;
+    if (b->use_graphs && cap == cudaStreamCaptureStatusNone) {
+        const BatchGraphKey key{n_iters, mode, b->cur, b->family, b->tile_words, batch_blocks(b)};
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                cudaError_t e = issue_batch(b, n_iters, b->cur);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                ok = e == cudaSuccess && e2 == cudaSuccess && g &&
+                     cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+                if (g) cudaGraphDestroy(g);
+            }
+            if (!ok) {
+                cudaGetLastError();
+                b->use_graphs = false;   // cooperative capture unavailable: launch directly
+            } else {
+                it = b->graphs.emplace(key, ex).first;
+            }
+        }
+        if (b->use_graphs) {
+            BB_CK(b, cudaGraphLaunch(it->second, b->stream));
+            b->launches += 1;
+            b->cur = end_cur;
+            return BP_OK;
+        }
+    }
+    BB_CK(b, issue_batch(b, n_iters, b->cur));
+    b->launches += 1;
+    b->cur = end_cur;
+    return BP_OK;
+}
+
+bp_status bp_batch_sync(bp_batch b) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_sync: NULL batch");
+    BB_CK(b, cudaStreamSynchronize(b->stream));
+    int flag = 0;
+    BB_CK(b, cudaMemcpy(&flag, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        BB_CK(b, cudaMemset(b->d_status, 0, sizeof(int)));
+        return bfail(b, BP_ERR_TIMEOUT, "the grid barrier of the batch kernel gave up waiting (status " +
+                                            std::to_string(flag) + ")");
+    }
+    return BP_OK;
+}
+
+bp_status bp_batch_beliefs(bp_batch b, int k, void *dev_out, int32_t *dev_map) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_beliefs: NULL batch");
+    b->err.clear();
+    if (k < 0 || k >= b->n || !dev_out) return bfail(b, BP_ERR_ARG, "bp_batch_beliefs: bad index or NULL output");
+    if (bp_status st = materialize_batch(b)) return st;
+    const MrfHost &m = b->mrfs[k];
+    const GridDims d{m.W, m.H, m.M, m.Mp, (long long)m.W * m.H * m.Mp};
+    if (b->dtype == BP_F32)
+        BB_CK(b, launch_beliefs_f32((const float *)m.unary, (const float *)m.msg[b->cur], d, 0, (float *)dev_out, dev_map,
+                                    b->stream));
+    else
+        BB_CK(b, launch_beliefs_i32((const int32_t *)m.unary, (const int32_t *)m.msg[b->cur], d, (int32_t *)dev_out,
+                                    dev_map, b->stream));
+    b->launches += 1;
+    return BP_OK;
+}
+
+bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_get_messages: NULL batch");
+    b->err.clear();
+    if (k < 0 || k >= b->n || !dev_planes) return bfail(b, BP_ERR_ARG, "bp_batch_get_messages: bad index or NULL output");
+    if (bp_status st = materialize_batch(b)) return st;
+    const MrfHost &m = b->mrfs[k];
+    BB_CK(b, launch_unpad_copy(m.msg[b->cur], dev_planes, 4LL * m.W * m.H, m.M, m.Mp, b->stream));
+    b->launches += 1;
+    return BP_OK;
+}
+
+// Project-written autotuner: times every (family, tile) candidate on this
+// batch for n_iters iterations (after one warm-up run each), keeps the
+// fastest, and records it in a cache file keyed by the batch's (Mp, T)
+// classes and size (path: $BP_AUTOTUNE_CACHE, if set).  Leaves the messages
+// reset to the uniform state.
+bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_autotune: NULL batch");
+    b->err.clear();
+    if (n_iters < 1) return bfail(b, BP_ERR_ARG, "bp_batch_autotune: n_iters < 1");
+    std::ostringstream sig;
+    long long words = 0;
+    std::map<std::pair<int, int>, long long> classes;
+    for (auto &m : b->mrfs) {
+        classes[{m.Mp, m.Teff}] += (long long)m.W * m.H;
+        words += (long long)m.W * m.H * m.Mp;
+    }
+    sig << (b->dtype == BP_I32 ? "i32" : "f32") << ":m" << mode << ":w" << (int)std::log2((double)words + 1);
+    for (auto &kv : classes) sig << ":" << kv.first.first << "x" << kv.first.second;
+    const char *cache = std::getenv("BP_AUTOTUNE_CACHE");
+    if (cache) {
+        std::ifstream in(cache);
+        std::string key;
+        int fam, tile;
+        float ms;
+        while (in >> key >> fam >> tile >> ms)
+            if (key == sig.str()) {
+                if (bp_status st = bp_batch_set_tiling(b, fam, tile)) return st;
+                if (host_best_ms) *host_best_ms = ms;
+                return bp_batch_reset_messages(b);
+            }
+    }
+    const int fams[] = {1, 2};
+    const int tiles[] = {4096, 16384, 65536};
+    cudaEvent_t e0, e1;
+    BB_CK(b, cudaEventCreate(&e0));
+    BB_CK(b, cudaEventCreate(&e1));
+    float best = 3e38f;
+    int best_f = b->family, best_t = b->tile_words;
+    bp_status st = BP_OK;
+    for (int f : fams)
+        for (int t : tiles) {
+            if (st) break;
+            st = bp_batch_set_tiling(b, f, t);
+            if (!st) st = bp_batch_reset_messages(b);
+            if (!st) st = bp_batch_iterate(b, n_iters, mode);   // warm-up (and graph capture)
+            if (!st && cudaEventRecord(e0, b->stream) != cudaSuccess) st = BP_ERR_CUDA;
+            if (!st) st = bp_batch_iterate(b, n_iters, mode);
+            if (!st && cudaEventRecord(e1, b->stream) != cudaSuccess) st = BP_ERR_CUDA;
+            if (!st) st = bp_batch_sync(b);
+            float ms = 0.f;
+            if (!st) cudaEventElapsedTime(&ms, e0, e1);
+            if (!st && ms < best) { best = ms; best_f = f; best_t = t; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st == BP_ERR_CUDA ? bfail(b, st, "bp_batch_autotune: timing failed") : st;
+    if (bp_status s2 = bp_batch_set_tiling(b, best_f, best_t)) return s2;
+    if (cache) {
+        std::ofstream o(cache, std::ios::app);
+        o << sig.str() << " " << best_f << " " << best_t << " " << best / n_iters << "\n";
+    }
+    if (host_best_ms) *host_best_ms = best / n_iters;
+    return bp_batch_reset_messages(b);
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// Device-side descriptors and launch interface of the batched O(mM) kernel.
+// Internal; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bp_internal.h"
+
+namespace bpg {
+
+struct BatchMrf {
+    const void *unary;      // [H][W][Mp]
+    void *msg[2];           // two [4][H][W][Mp] message states
+    long long plane;        // H * W * Mp
+    int W, H, M, Mp;
+    int T;                  // effective band half-width (<= kTMaxFast)
+    float wf[2 * kTMaxFast + 1];    // f(d) - fbar (sum-product)
+    float fbar;
+    int32_t wi[2 * kTMaxFast + 1];  // E(d) (min-sum)
+    int32_t ebar;
+};
+
+struct BatchItem {
+    int mrf;
+    int node0;
+    int count;
+};
+
+struct BatchArgs {
+    const BatchMrf *mrfs;
+    const BatchItem *items;
+    int n_items;
+    int n_iters;
+    int start_buf;              // iteration t reads msg[(start_buf + t) & 1]
+    unsigned *bar_count;        // grid barrier: arrivals, generation
+    unsigned *bar_gen;
+    int extra_arrivals;         // 0; > 0 makes the barrier wait for blocks that never come
+    unsigned long long limit_ns;
+    int *status;
+};
+
+// Launch one persistent cooperative batch kernel (family 1 or 2).
+cudaError_t launch_batch(const BatchArgs &a, int family, bool min_sum, int blocks, cudaStream_t s);
+// Largest co-resident grid for that kernel.
+int batch_max_blocks(int family, bool min_sum);
+// Groups per block (nodes in flight) of a family for a padded label count.
+int batch_lanes_per_node(int family, int Mp);
+
+}  // namespace bpg
