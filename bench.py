@@ -171,6 +171,20 @@ def oracle_sample(cfg, stereo_obj, target_s=10.0):
 
 # ------------------------------------------------------------------ GPU arm ----
 
+def aggregate_over_ranks(elapsed_s, units_local, world, device=None):
+    """Whole-job numbers for N independent replicas: the slowest rank's time
+    and the units of all ranks (every rank returns the same pair)."""
+    if world <= 1:
+        return elapsed_s, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args, cfg, rank, world):
     import torch
     from paper_1010_0012_gb300 import bp
@@ -223,14 +237,12 @@ def run_ours(args, cfg, rank, world):
     launches = G.launches - launches0
     elapsed = t0.elapsed_time(t1) / 1e3
     band_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    elapsed, units_all = aggregate_over_ranks(elapsed, units_step * args.steps, world, device="cuda")
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
         dist.barrier()
     torch.cuda.synchronize()
-    out = {"elapsed": elapsed, "units": units_step * args.steps * world, "launches": launches,
+    out = {"elapsed": elapsed, "units": units_all, "launches": launches,
            "band_launch_s": band_s / (args.steps * K), "clocks": clk.summary()}
 
     # end to end through the public API: pinned host unary in, MAP out, every step
