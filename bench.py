@@ -267,7 +267,8 @@ def run_ours(args, cfg, rank, world):
     # O(M^2) baselines on the same grid and state, timed per iteration
     if not args.no_baselines:
         base = {}
-        for name, kind in (("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE), ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC)):
+        for name, kind in (("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE), ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC),
+                           ("dense_bf16_tcgen05_fused", bp.BP_DENSE_BF16_TC_FUSED)):
             try:
                 G.reset()
                 n_it = 3

@@ -66,8 +66,12 @@ typedef enum { BP_F32 = 0, BP_I32 = 1 } bp_dtype;
 /* O(M^2) baselines of the standard update (Eq. 2 / Eq. 9), for comparison. */
 typedef enum {
     BP_DENSE_CUDA_CORE = 0, /* FP32 sum-product or int32 min-sum, CUDA cores          */
-    BP_DENSE_BF16_TC = 1    /* sum-product as a (nodes*4 x M)(M x M) tcgen05 GEMM,    */
-                            /* BF16 operands, FP32 accumulate, normalising epilogue   */
+    BP_DENSE_BF16_TC = 1,   /* sum-product as a (nodes*4 x M)(M x M) tcgen05 GEMM,    */
+                            /* BF16 operands, FP32 accumulate, normalising epilogue;  */
+                            /* h rows packed to HBM by a separate kernel (M 33..128)  */
+    BP_DENSE_BF16_TC_FUSED = 2 /* the same GEMM with h formed on chip from one read  */
+                            /* of the node's vectors (same HBM bytes as the O(mM)     */
+                            /* update; M 33..128)                                     */
 } bp_dense_kind;
 
 /* Create a handle for an H x W grid with M labels (2 <= M <= 1024,

@@ -21,7 +21,7 @@ BP_OK, BP_ERR_ARG, BP_ERR_STATE, BP_ERR_CUDA, BP_ERR_OOM, BP_ERR_POTENTIAL, BP_E
 BP_SUM, BP_MAX, BP_LOG, BP_RECORD = 0, 1, 2, 4
 BP_SYNC, BP_REDBLACK = 0, 1
 BP_F32, BP_I32 = 0, 1
-BP_DENSE_CUDA_CORE, BP_DENSE_BF16_TC = 0, 1
+BP_DENSE_CUDA_CORE, BP_DENSE_BF16_TC, BP_DENSE_BF16_TC_FUSED = 0, 1, 2
 STATUS_NAMES = {0: "BP_OK", 1: "BP_ERR_ARG", 2: "BP_ERR_STATE", 3: "BP_ERR_CUDA", 4: "BP_ERR_OOM",
                 5: "BP_ERR_POTENTIAL", 6: "BP_ERR_TIMEOUT", 7: "BP_ERR_UNSUPPORTED"}
 SCHEDULES = {"sync": BP_SYNC, "redblack": BP_REDBLACK}

@@ -417,9 +417,9 @@ bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind) {
     if (bp_status st = bpg_check_device(h)) return st;
     if (bp_status st = materialize(h, false)) return st;
     h->recorded = false;
-    if (kind == BP_DENSE_BF16_TC) {
+    if (kind == BP_DENSE_BF16_TC || kind == BP_DENSE_BF16_TC_FUSED) {
         if (h->dtype != BP_F32) return fail(h, BP_ERR_ARG, "bp_iterate_dense: the tensor-core baseline is sum-product");
-        return bpg_dense_tc_iterate(h, n_iters);
+        return bpg_dense_tc_iterate_kind(h, n_iters, kind == BP_DENSE_BF16_TC_FUSED);
     }
     if (kind != BP_DENSE_CUDA_CORE) return fail(h, BP_ERR_ARG, "bp_iterate_dense: unknown kind");
     // the full M x M table, F[x_i][x_j] (f, or E for min-sum)

@@ -96,6 +96,7 @@ cudaError_t bpg_issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int &c
 bp_status bpg_record_forward(bp_ctx *h, int n_iters);   // bp_backward.cu
 void bpg_free_extras(bp_ctx *h);                         // bp_backward.cu
 bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters);  // dense_tc.cu
+bp_status bpg_dense_tc_iterate_kind(bp_ctx *h, int n_iters, bool fused);
 void bpg_free_tc(bp_ctx *h);                             // dense_tc.cu
 
 namespace bpg {

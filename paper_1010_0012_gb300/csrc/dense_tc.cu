@@ -158,7 +158,8 @@ struct TcCfg {
     static constexpr uint32_t kAStage = (uint32_t)kTileM * MP * 2;
     static constexpr uint32_t kBBytes = (uint32_t)MP * MP * 2;
     static constexpr uint32_t kTmemCols = 2 * MP;   // two accumulators
-    static constexpr size_t kSmem = 1024 + kBBytes + kStages * kAStage + 256;
+    static constexpr uint32_t kStage = 4 * 32 * 32 * 4;   // per epilogue warp: one 32 x 32 FP32 tile
+    static constexpr size_t kSmem = 1024 + kBBytes + kStages * kAStage + kStage + 256;
 };
 
 template <int MP>
@@ -170,7 +171,8 @@ dense_tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_co
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sB = smem;
     uint8_t *sA = smem + Cfg::kBBytes;
-    uint64_t *bars = (uint64_t *)(sA + kStages * Cfg::kAStage);
+    float *sStage = (float *)(sA + kStages * Cfg::kAStage);
+    uint64_t *bars = (uint64_t *)(sA + kStages * Cfg::kAStage + Cfg::kStage);
     uint64_t *full = bars;
     uint64_t *empty = bars + kStages;
     uint64_t *b_full = bars + 2 * kStages;
@@ -267,7 +269,6 @@ dense_tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_co
     } else if (warp >= 2) {
         // ----------------------------------------------------------- epilogue
         const int quad = warp & 3;                // TMEM lanes [32 quad, 32 quad + 32)
-        const int row_in_tile = quad * 32 + lane;
         long long i = 0;
         for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
             const int acc = (int)(i & 1);
@@ -291,16 +292,284 @@ dense_tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_co
                 for (int j = 0; j < 32; ++j) z += v[j];
             }
             const float inv = z > 0.f ? 1.f / z : 0.f;
-            const long long grow = t * kTileM + row_in_tile;
+            // Transpose each 32 x 32 chunk through this warp's shared tile (16-byte
+            // chunks XOR-swizzled by row) so that global stores are whole 128-byte
+            // row segments: 8 lanes per row, 4 rows per store instruction.
+            float *stg = sStage + (warp - 2) * 32 * 32;
+            const long long row0 = t * kTileM + quad * 32;
+            const int kk = lane & 7;
 #pragma unroll
             for (int c = 0; c < MP / 32; ++c) {
                 tmem_ld32(taddr + c * 32, v);
-                if (grow < rows) {
-                    float4 *dst = reinterpret_cast<float4 *>(out + grow * MP + c * 32);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        dst[j] = make_float4(v[4 * j] * inv, v[4 * j + 1] * inv, v[4 * j + 2] * inv, v[4 * j + 3] * inv);
+                for (int k = 0; k < 8; ++k)
+                    *reinterpret_cast<float4 *>(stg + lane * 32 + ((k ^ (lane & 7)) * 4)) =
+                        make_float4(v[4 * k] * inv, v[4 * k + 1] * inv, v[4 * k + 2] * inv, v[4 * k + 3] * inv);
+                __syncwarp();
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const int r = (lane >> 3) + 4 * p;
+                    const float4 x = *reinterpret_cast<const float4 *>(stg + r * 32 + ((kk ^ (r & 7)) * 4));
+                    if (row0 + r < rows) *reinterpret_cast<float4 *>(out + (row0 + r) * MP + c * 32 + kk * 4) = x;
                 }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused form: the same dense update with h formed on chip.  A tile is 32 sender
+// nodes x 4 directions = 128 rows; rows 32t..32t+31 hold h for direction t
+// (t = 0 left, 1 right, 2 up, 3 down), so TMEM lane quadrant t holds the 32
+// outgoing messages towards side t, which go to 32 consecutive slots of the
+// destination plane.  Warps 2-5 form h from one read of g and the four
+// incoming vectors of each node (exactly the bytes the O(mM) kernel reads) and
+// write it as BF16 into the swizzled A stage; warp 1 issues the MMAs; warps
+// 6-9 normalise and store.
+constexpr int kFusedThreads = 320;
+constexpr int kFusedNodes = 32;
+
+template <int MP>
+struct FusedCfg {
+    static constexpr int KB = MP / kBlockK;
+    static constexpr uint32_t kAStage = (uint32_t)kTileM * MP * 2;
+    static constexpr uint32_t kBBytes = (uint32_t)MP * MP * 2;
+    static constexpr uint32_t kTmemCols = 2 * MP;
+    static constexpr uint32_t kStage = 4 * 32 * 32 * 4;
+    static constexpr size_t kSmem = 1024 + kBBytes + kStages * kAStage + kStage + 256;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+template <int MP>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+dense_tc_fused_kernel(const __grid_constant__ CUtensorMap tmap_b, const float *__restrict__ g,
+                      const float *__restrict__ in, float *__restrict__ out, bpg::GridDims d, int *status) {
+    using Cfg = FusedCfg<MP>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sB = smem;
+    uint8_t *sA = smem + Cfg::kBBytes;
+    float *sStage = (float *)(sA + kStages * Cfg::kAStage);
+    uint64_t *bars = (uint64_t *)(sA + kStages * Cfg::kAStage + Cfg::kStage);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + kStages;
+    uint64_t *b_full = bars + 2 * kStages;
+    uint64_t *acc_full = b_full + 1;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = d.W, H = d.H;
+    const long long N = (long long)W * H;
+    const long long n_tiles = (N + kFusedNodes - 1) / kFusedNodes;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 128);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(b_full, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, Cfg::kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp >= 2 && warp < 6) {
+        // ------------------------------------------------ h producers (128 thr)
+        const int ptid = threadIdx.x - 64;
+        constexpr int CH = MP / 8;              // 8-label chunks per node
+        long long i = 0;
+        for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+            const int s = (int)(i % kStages);
+            const uint32_t ph = (uint32_t)((i / kStages) & 1);
+            if (!mbar_wait(&empty[s], ph ^ 1, abort_flag)) {
+                *abort_flag = 1;
+                atomicExch(status, 111);
+                break;
+            }
+            uint8_t *As = sA + s * Cfg::kAStage;
+            const long long n0 = t * kFusedNodes;
+            for (int u = ptid; u < kFusedNodes * CH; u += 128) {
+                const int nl = u / CH, ch = u - nl * CH;
+                const long long n = n0 + nl;
+                float gv[8], m[4][8];
+                bool has[4] = {false, false, false, false};
+                if (n < N) {
+                    const int r = (int)(n / W), c = (int)(n - (long long)r * W);
+                    has[0] = c > 0; has[1] = c < W - 1; has[2] = r > 0; has[3] = r < H - 1;
+                    const float *gp = g + n * MP + ch * 8;
+                    const float4 g0 = __ldg(reinterpret_cast<const float4 *>(gp));
+                    const float4 g1 = __ldg(reinterpret_cast<const float4 *>(gp) + 1);
+                    gv[0] = g0.x; gv[1] = g0.y; gv[2] = g0.z; gv[3] = g0.w;
+                    gv[4] = g1.x; gv[5] = g1.y; gv[6] = g1.z; gv[7] = g1.w;
+#pragma unroll
+                    for (int sd = 0; sd < 4; ++sd) {
+                        if (has[sd]) {
+                            const float *mp = in + sd * d.plane + n * MP + ch * 8;
+                            const float4 a = __ldg(reinterpret_cast<const float4 *>(mp));
+                            const float4 b = __ldg(reinterpret_cast<const float4 *>(mp) + 1);
+                            m[sd][0] = a.x; m[sd][1] = a.y; m[sd][2] = a.z; m[sd][3] = a.w;
+                            m[sd][4] = b.x; m[sd][5] = b.y; m[sd][6] = b.z; m[sd][7] = b.w;
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) m[sd][k] = 1.f;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        gv[k] = 0.f;
+#pragma unroll
+                        for (int sd = 0; sd < 4; ++sd) m[sd][k] = 1.f;
+                    }
+                }
+#pragma unroll
+                for (int td = 0; td < 4; ++td) {
+                    float h[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        float p = has[td] ? gv[k] : 0.f;
+#pragma unroll
+                        for (int sd = 0; sd < 4; ++sd)
+                            if (sd != td) p *= m[sd][k];
+                        h[k] = p;
+                    }
+                    const int row = td * 32 + nl;
+                    const int kb = ch >> 3, cc = ch & 7;
+                    const uint32_t off = (uint32_t)kb * (kTileM * 128) + (uint32_t)(row >> 3) * 1024 +
+                                         (uint32_t)(row & 7) * 128 + (uint32_t)((cc ^ (row & 7)) * 16);
+                    *reinterpret_cast<uint4 *>(As + off) =
+                        make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                                   pack_bf16x2(h[6], h[7]));
+                }
+            }
+            // make the generic-proxy writes visible to the tensor core's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[s]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------------ MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(kTileM, MP);
+        mbar_expect_tx(b_full, Cfg::kBBytes);
+        for (int kb = 0; kb < Cfg::KB; ++kb) tma_load_2d(sB + kb * MP * 128, &tmap_b, b_full, kb * kBlockK, 0);
+        bool ok = mbar_wait(b_full, 0, abort_flag);
+        long long i = 0;
+        int last_acc = -1;
+        uint32_t last_aph = 0;
+        if (ok) {
+            for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+                const int s = (int)(i % kStages);
+                const uint32_t ph = (uint32_t)((i / kStages) & 1);
+                const int acc = (int)(i & 1);
+                const uint32_t aph = (uint32_t)((i >> 1) & 1);
+                if (!mbar_wait(&acc_empty[acc], aph ^ 1, abort_flag) || !mbar_wait(&full[s], ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + s * Cfg::kAStage);
+                const uint32_t b0 = smem_u32(sB);
+#pragma unroll
+                for (int kb = 0; kb < Cfg::KB; ++kb)
+#pragma unroll
+                    for (int k = 0; k < kBlockK / 16; ++k)
+                        umma_bf16(tmem_base + (uint32_t)(acc * MP), sw128_desc(a0 + kb * kTileM * 128 + k * 32),
+                                  sw128_desc(b0 + kb * MP * 128 + k * 32), idesc, (kb | k) != 0);
+                umma_commit(&empty[s]);
+                umma_commit(&acc_full[acc]);
+                last_acc = acc;
+                last_aph = aph;
+            }
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(status, 112);
+        }
+        mbar_wait(b_full, 0, nullptr);
+        if (last_acc >= 0) mbar_wait(&acc_full[last_acc], last_aph, nullptr);
+    } else if (warp >= 6) {
+        // --------------------------------------------- normalise and store
+        const int quad = warp & 3;                // TMEM lanes of direction `quad`
+        const int dr = (quad == 2) ? -1 : (quad == 3) ? 1 : 0;
+        const int dc = (quad == 0) ? -1 : (quad == 1) ? 1 : 0;
+        const long long delta = (long long)dr * W + dc;
+        float *dst_plane = out + (long long)(quad ^ 1) * d.plane;
+        float *stg = sStage + (warp - 6) * 32 * 32;
+        const int kk = lane & 7;
+        long long i = 0;
+        for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+            const int acc = (int)(i & 1);
+            const uint32_t aph = (uint32_t)((i >> 1) & 1);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], aph, abort_flag));
+            if (!ok) {
+                if (lane == 0) {
+                    *abort_flag = 1;
+                    atomicExch(status, 113);
+                }
+                break;
+            }
+            tc_fence_after();
+            const long long n0 = t * kFusedNodes;
+            // rows of this warp whose message exists (sender inside, neighbour present)
+            bool mine = false;
+            {
+                const long long n = n0 + lane;
+                if (n < N) {
+                    const int r = (int)(n / W), c = (int)(n - (long long)r * W);
+                    mine = (quad == 0) ? c > 0 : (quad == 1) ? c < W - 1 : (quad == 2) ? r > 0 : r < H - 1;
+                }
+            }
+            const unsigned valid = __ballot_sync(0xffffffffu, mine);
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * MP);
+            float v[32];
+            float z = 0.f;
+#pragma unroll
+            for (int c = 0; c < MP / 32; ++c) {
+                tmem_ld32(taddr + c * 32, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) z += v[j];
+            }
+            const float inv = z > 0.f ? 1.f / z : 0.f;
+#pragma unroll
+            for (int c = 0; c < MP / 32; ++c) {
+                tmem_ld32(taddr + c * 32, v);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    *reinterpret_cast<float4 *>(stg + lane * 32 + ((k ^ (lane & 7)) * 4)) =
+                        make_float4(v[4 * k] * inv, v[4 * k + 1] * inv, v[4 * k + 2] * inv, v[4 * k + 3] * inv);
+                __syncwarp();
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const int r = (lane >> 3) + 4 * p;
+                    const float4 x = *reinterpret_cast<const float4 *>(stg + r * 32 + ((kk ^ (r & 7)) * 4));
+                    if ((valid >> r) & 1u)
+                        *reinterpret_cast<float4 *>(dst_plane + (n0 + r + delta) * MP + c * 32 + kk * 4) = x;
+                }
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -407,9 +676,29 @@ cudaError_t launch_gemm(const TcState &st, float *out, long long rows, int *stat
     return cudaGetLastError();
 }
 
+template <int MP>
+cudaError_t launch_fused(const TcState &st, const float *g, const float *in, float *out, const bpg::GridDims &d,
+                         int *status, cudaStream_t s) {
+    using Cfg = FusedCfg<MP>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(dense_tc_fused_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long tiles = ((long long)d.W * d.H + kFusedNodes - 1) / kFusedNodes;
+    int grid = bpg::device_sm_count();
+    if (grid > tiles) grid = (int)tiles;
+    dense_tc_fused_kernel<MP><<<grid, kFusedThreads, Cfg::kSmem, s>>>(st.map_b, g, in, out, d, status);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters) {
+bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters) { return bpg_dense_tc_iterate_kind(h, n_iters, false); }
+
+bp_status bpg_dense_tc_iterate_kind(bp_ctx *h, int n_iters, bool fused) {
     if (h->Mp != 64 && h->Mp != 128)
         return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_iterate_dense: the tensor-core baseline serves 33 <= M <= 128");
     const long long rows = 4LL * h->W * h->H;
@@ -445,6 +734,18 @@ bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters) {
         h->tc_ready = true;
     }
     const TcState &st = *(const TcState *)h->tc_maps;
+    if (fused) {
+        for (int it = 0; it < n_iters; ++it) {
+            cudaError_t e = Mp == 128 ? launch_fused<128>(st, (const float *)h->unary, (const float *)h->msg[h->cur],
+                                                          (float *)h->msg[h->cur ^ 1], h->dims, h->d_status, h->stream)
+                                      : launch_fused<64>(st, (const float *)h->unary, (const float *)h->msg[h->cur],
+                                                         (float *)h->msg[h->cur ^ 1], h->dims, h->d_status, h->stream);
+            if (e != cudaSuccess) return bpg_cuda_fail(h, e, "fused tensor-core launch");
+            h->launches += 1;
+            h->cur ^= 1;
+        }
+        return BP_OK;
+    }
     for (int it = 0; it < n_iters; ++it) {
         const long long n = (long long)h->W * h->H * (Mp / 4);
         hpack_kernel<<<bpg::grid_for(n, 256), 256, 0, h->stream>>>((const float *)h->unary, (const float *)h->msg[h->cur],

@@ -16,13 +16,14 @@ pytestmark = pytest.mark.gpu
 TOL = 2.0 ** -6 * 1.02
 
 
-def _one_step(W, Hh, M, T, alpha, seed):
+def _one_step(W, Hh, M, T, alpha, seed, fused=False):
     from paper_1010_0012_gb300 import bp
     rng = np.random.default_rng(seed)
     g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
     planes0 = H.random_planes_sum(W, Hh, M, rng)
     tab, fbar = wl.pair_table_f32(alpha, T)
-    bel, mp, msgs = H.run_gpu_sum(g, tab, T, fbar, 1, planes0=planes0, dense=bp.BP_DENSE_BF16_TC)
+    kind = bp.BP_DENSE_BF16_TC_FUSED if fused else bp.BP_DENSE_BF16_TC
+    bel, mp, msgs = H.run_gpu_sum(g, tab, T, fbar, 1, planes0=planes0, dense=kind)
     F = H.oracle_F_from_table(tab, T, fbar, M)
     p64, _ = grid.grid_sum_product(g.astype(np.float64), F, 1, planes0=planes0)
     src, dst, side, rr, cc = grid.grid_edges(W, Hh)
@@ -32,18 +33,22 @@ def _one_step(W, Hh, M, T, alpha, seed):
     return float(rel.max())
 
 
-@pytest.mark.parametrize("W,Hh,M,T", [(9, 7, 128, 4), (13, 5, 64, 3), (11, 6, 100, 4), (200, 100, 128, 4)])
-def test_one_iteration_within_bf16_bound(W, Hh, M, T):
-    err = _one_step(W, Hh, M, T, 0.5, seed=W * Hh + M)
+@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("W,Hh,M,T", [(9, 7, 128, 4), (13, 5, 64, 3), (11, 6, 100, 4), (200, 100, 128, 4),
+                                      (1, 37, 128, 2), (45, 1, 64, 2)])
+def test_one_iteration_within_bf16_bound(W, Hh, M, T, fused):
+    err = _one_step(W, Hh, M, T, 0.5, seed=W * Hh + M, fused=fused)
     assert err <= TOL, f"max relative error {err:.4e} > {TOL:.4e}"
 
 
-def test_several_iterations_map_agrees_where_clear():
+@pytest.mark.parametrize("fused", [False, True])
+def test_several_iterations_map_agrees_where_clear(fused):
     from paper_1010_0012_gb300 import bp
     cfg = wl.small_config("tc", 40, 24, 128, 4, alpha=0.5, structure="slanted", seed=3)
     st, g, _ = H.stereo_inputs(cfg)
     tab, fbar = wl.pair_table_f32(cfg.alpha, cfg.T)
-    bel, mp, _ = H.run_gpu_sum(g, tab, cfg.T, fbar, 8, dense=bp.BP_DENSE_BF16_TC)
+    bel, mp, _ = H.run_gpu_sum(g, tab, cfg.T, fbar, 8,
+                               dense=bp.BP_DENSE_BF16_TC_FUSED if fused else bp.BP_DENSE_BF16_TC)
     F = H.oracle_F_from_table(tab, cfg.T, fbar, cfg.M)
     _, b64 = grid.grid_sum_product(g.astype(np.float64), F, 8)
     top2 = np.sort(b64, -1)[..., -2:]
@@ -64,3 +69,18 @@ def test_unsupported_label_count_is_reported():
         G.iterate_dense(1, bp.BP_DENSE_BF16_TC)
     assert ei.value.status == bp.BP_ERR_UNSUPPORTED
     G.close()
+
+
+def test_fused_and_packed_forms_agree_bit_for_bit():
+    """Both forms round the same h to BF16 and run the same MMAs, so the
+    messages agree exactly."""
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(17)
+    W, Hh, M, T = 33, 21, 128, 4
+    g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
+    p0 = H.random_planes_sum(W, Hh, M, rng)
+    tab, fbar = wl.pair_table_f32(0.5, T)
+    _, _, a = H.run_gpu_sum(g, tab, T, fbar, 2, planes0=p0, dense=bp.BP_DENSE_BF16_TC)
+    _, _, b = H.run_gpu_sum(g, tab, T, fbar, 2, planes0=p0, dense=bp.BP_DENSE_BF16_TC_FUSED)
+    src, dst, side, rr, cc = grid.grid_edges(W, Hh)
+    np.testing.assert_array_equal(a[side, rr, cc], b[side, rr, cc])
