@@ -333,11 +333,14 @@ dense_tc_gemm_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_co
 // nodes x 4 directions = 128 rows; rows 32t..32t+31 hold h for direction t
 // (t = 0 left, 1 right, 2 up, 3 down), so TMEM lane quadrant t holds the 32
 // outgoing messages towards side t, which go to 32 consecutive slots of the
-// destination plane.  Warps 2-5 form h from one read of g and the four
+// destination plane.  Warps 2-9 form h from one read of g and the four
 // incoming vectors of each node (exactly the bytes the O(mM) kernel reads) and
 // write it as BF16 into the swizzled A stage; warp 1 issues the MMAs; warps
-// 6-9 normalise and store.
-constexpr int kFusedThreads = 320;
+// 10-13 normalise and store.
+constexpr int kFusedProducerWarps = 8;
+constexpr int kFusedProducers = 32 * kFusedProducerWarps;
+constexpr int kFusedEpiWarp0 = 2 + kFusedProducerWarps;          // first epilogue warp
+constexpr int kFusedThreads = 32 * (kFusedEpiWarp0 + 4);
 constexpr int kFusedNodes = 32;
 
 template <int MP>
@@ -381,7 +384,7 @@ dense_tc_fused_kernel(const __grid_constant__ CUtensorMap tmap_b, const float *_
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 128);
+            mbar_init(&full[s], kFusedProducers);
             mbar_init(&empty[s], 1);
         }
         mbar_init(b_full, 1);
@@ -398,8 +401,8 @@ dense_tc_fused_kernel(const __grid_constant__ CUtensorMap tmap_b, const float *_
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp >= 2 && warp < 6) {
-        // ------------------------------------------------ h producers (128 thr)
+    if (warp >= 2 && warp < kFusedEpiWarp0) {
+        // ------------------------------------------------------- h producers
         const int ptid = threadIdx.x - 64;
         constexpr int CH = MP / 8;              // 8-label chunks per node
         long long i = 0;
@@ -413,7 +416,7 @@ dense_tc_fused_kernel(const __grid_constant__ CUtensorMap tmap_b, const float *_
             }
             uint8_t *As = sA + s * Cfg::kAStage;
             const long long n0 = t * kFusedNodes;
-            for (int u = ptid; u < kFusedNodes * CH; u += 128) {
+            for (int u = ptid; u < kFusedNodes * CH; u += kFusedProducers) {
                 const int nl = u / CH, ch = u - nl * CH;
                 const long long n = n0 + nl;
                 float gv[8], m[4][8];
@@ -511,14 +514,14 @@ dense_tc_fused_kernel(const __grid_constant__ CUtensorMap tmap_b, const float *_
         }
         mbar_wait(b_full, 0, nullptr);
         if (last_acc >= 0) mbar_wait(&acc_full[last_acc], last_aph, nullptr);
-    } else if (warp >= 6) {
+    } else if (warp >= kFusedEpiWarp0) {
         // --------------------------------------------- normalise and store
         const int quad = warp & 3;                // TMEM lanes of direction `quad`
         const int dr = (quad == 2) ? -1 : (quad == 3) ? 1 : 0;
         const int dc = (quad == 0) ? -1 : (quad == 1) ? 1 : 0;
         const long long delta = (long long)dr * W + dc;
         float *dst_plane = out + (long long)(quad ^ 1) * d.plane;
-        float *stg = sStage + (warp - 6) * 32 * 32;
+        float *stg = sStage + (warp - kFusedEpiWarp0) * 32 * 32;
         const int kk = lane & 7;
         long long i = 0;
         for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
