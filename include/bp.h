@@ -229,6 +229,15 @@ const char *bp_batch_last_error(bp_batch b);
 long long bp_batch_launch_count(bp_batch b);
 void bp_batch_destroy(bp_batch b);
 
+/* How bp_iterate issues the linear sum-product and min-sum updates:
+ * 0: one launch per iteration (two per red-black iteration);
+ * 1: ONE persistent cooperative launch for the whole call, with a bounded grid
+ *    barrier between iterations (half-steps), where served (16 < Mp <= 256
+ *    after padding, T <= 8); otherwise as 0;
+ * -1 (default): 1 when one iteration moves under 96 MB (launch latency, not
+ *    bandwidth, bounds such grids), else 0.  Results are identical. */
+bp_status bp_set_persistent(bp_handle h, int mode);
+
 /* Number of kernel launches the library issued on this handle so far. */
 long long bp_launch_count(bp_handle h);
 

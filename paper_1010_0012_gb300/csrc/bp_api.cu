@@ -13,8 +13,16 @@
 #include <vector>
 
 #include "../../include/bp.h"
+#include "bp_batch_internal.h"
 #include "bp_internal.h"
 #include "bp_ctx.h"
+
+namespace bpg {
+cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
+cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
+int batch_max_blocks_sum(int family);
+int batch_max_blocks_min(int family);
+}  // namespace bpg
 
 using namespace bpg;
 
@@ -150,14 +158,100 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
     return cudaSuccess;
 }
 
-// Run n iterations, through a cached CUDA graph when possible.  `per_iter`
-// (nullable) is called after every iteration with the iteration index (used
-// by recording); recording runs are issued directly.
+// ---- one persistent launch for a whole bp_iterate call -----------------------
+// Served for the linear sum-product and min-sum updates with 16 <= Mp <= 256
+// and T <= 8 (the label classes of the persistent kernel).  Automatic mode
+// takes it when one iteration moves less than 96 MB, where launch latency
+// rather than HBM bandwidth bounds the per-launch form.
+static bool persistent_served(const bp_ctx *h, int mode) {
+    return h->fast && !(mode & BP_LOG) && h->Mp >= 16 && h->Mp <= 256 && h->Teff <= kTMaxFast;
+}
+
+static bool use_persistent(const bp_ctx *h, int mode) {
+    if (h->persistent == 0 || !persistent_served(h, mode)) return false;
+    if (h->persistent == 1) return true;
+    const double bytes = ((double)h->W * h->H * h->M + 8.0 * h->W * h->H * h->M) * 4.0;
+    return bytes < 96e6;
+}
+
+static bp_status persistent_setup(bp_ctx *h) {
+    if (h->p_ready) return BP_OK;
+    BatchMrf m{};
+    m.unary = h->unary;
+    m.msg[0] = h->msg[0];
+    m.msg[1] = h->msg[1];
+    m.plane = h->dims.plane;
+    m.W = h->W; m.H = h->H; m.M = h->M; m.Mp = h->Mp; m.T = h->Teff;
+    if (h->dtype == BP_F32) {
+        for (int i = 0; i < 2 * h->Teff + 1; ++i) m.wf[i] = h->wf[i];
+        m.fbar = h->fbarf;
+    } else {
+        for (int i = 0; i < 2 * h->Teff + 1; ++i) m.wi[i] = h->wi[i];
+        m.ebar = h->ebar;
+    }
+    if (bp_status st = ensure_buffer(h, &h->p_mrf, sizeof(BatchMrf), "persistent descriptor")) return st;
+    if (bp_status st = ensure_buffer(h, &h->p_bar, 2 * sizeof(unsigned), "barrier words")) return st;
+    const int maxb = h->dtype == BP_I32 ? batch_max_blocks_min(1) : batch_max_blocks_sum(1);
+    const int gpb = kBlock / batch_lanes_per_node(1, h->Mp);
+    for (int sched = 0; sched < 2; ++sched) {
+        const int nslots = sched == BP_REDBLACK ? ((h->W + 1) / 2) * h->H : h->W * h->H;
+        // about four items per resident block, whole node groups per item
+        int tile = (nslots + 4 * maxb - 1) / (4 * maxb);
+        tile = std::max(gpb, (tile + gpb - 1) / gpb * gpb);
+        std::vector<BatchItem> items;
+        for (int s0 = 0; s0 < nslots; s0 += tile) items.push_back(BatchItem{0, s0, std::min(tile, nslots - s0)});
+        if (h->p_items[sched]) { cudaFree(h->p_items[sched]); h->p_items[sched] = nullptr; }
+        if (bp_status st = ensure_buffer(h, &h->p_items[sched], items.size() * sizeof(BatchItem), "persistent items"))
+            return st;
+        BP_CK(h, cudaMemcpyAsync(h->p_items[sched], items.data(), items.size() * sizeof(BatchItem),
+                                 cudaMemcpyHostToDevice, h->stream));
+        h->p_nitems[sched] = (int)items.size();
+        BP_CK(h, cudaStreamSynchronize(h->stream));   // the host vector dies here
+    }
+    BP_CK(h, cudaMemcpyAsync(h->p_mrf, &m, sizeof(BatchMrf), cudaMemcpyHostToDevice, h->stream));
+    BP_CK(h, cudaMemsetAsync(h->p_bar, 0, 2 * sizeof(unsigned), h->stream));
+    BP_CK(h, cudaStreamSynchronize(h->stream));
+    h->p_ready = true;
+    return BP_OK;
+}
+
+static cudaError_t issue_persistent(bp_ctx *h, int n, int sched, int cur) {
+    BatchArgs a{};
+    a.mrfs = (const BatchMrf *)h->p_mrf;
+    a.items = (const BatchItem *)h->p_items[sched == BP_REDBLACK ? 1 : 0];
+    a.n_items = h->p_nitems[sched == BP_REDBLACK ? 1 : 0];
+    a.n_iters = n;
+    a.start_buf = cur;
+    a.redblack = sched == BP_REDBLACK ? 1 : 0;
+    a.bar_count = (unsigned *)h->p_bar;
+    a.bar_gen = (unsigned *)h->p_bar + 1;
+    a.extra_arrivals = 0;
+    a.limit_ns = 2000000000ull;
+    a.status = h->d_status;
+    cudaError_t e = cudaMemsetAsync(h->p_bar, 0, sizeof(unsigned), h->stream);
+    if (e != cudaSuccess) return e;
+    const int maxb = h->dtype == BP_I32 ? batch_max_blocks_min(1) : batch_max_blocks_sum(1);
+    const int blocks = std::max(1, std::min(maxb, a.n_items));
+    return h->dtype == BP_I32 ? launch_batch_min(a, 1, blocks, h->stream) : launch_batch_sum(a, 1, blocks, h->stream);
+}
+
+// Run n iterations, through a cached CUDA graph when possible.
 static bp_status run_iterations(bp_ctx *h, int n, int mode, int sched) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     BP_CK(h, cudaStreamIsCapturing(h->stream, &cap));
-    const bool use_graph = h->use_graphs && cap == cudaStreamCaptureStatusNone && n > 1;
+    const bool persist = use_persistent(h, mode);
+    if (persist) {
+        if (bp_status st = persistent_setup(h)) return st;
+    }
+    const bool use_graph = h->use_graphs && cap == cudaStreamCaptureStatusNone && (n > 1 || persist);
     if (!use_graph) {
+        if (persist) {
+            cudaError_t e = issue_persistent(h, n, sched, h->cur);
+            if (e != cudaSuccess) return cuda_fail(h, e, "persistent O(mM) launch");
+            h->launches += 1;
+            if (sched != BP_REDBLACK) h->cur = (h->cur + n) & 1;
+            return BP_OK;
+        }
         for (int it = 0; it < n; ++it) {
             int count = 0;
             cudaError_t e = issue_iteration(h, mode, sched, h->cur, count);
@@ -166,14 +260,20 @@ static bp_status run_iterations(bp_ctx *h, int n, int mode, int sched) {
         }
         return BP_OK;
     }
-    const GraphKey key{n, mode, sched, h->cur, h->layout.L, h->layout.C, h->blocks_override};
+    const GraphKey key{n, mode, sched, h->cur, h->layout.L, h->layout.C, h->blocks_override, persist ? 1 : 0};
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;
         BP_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         int cur = h->cur, count = 0;
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < n && e == cudaSuccess; ++k) e = issue_iteration(h, mode, sched, cur, count);
+        if (persist) {
+            e = issue_persistent(h, n, sched, cur);
+            count = 1;
+            if (sched != BP_REDBLACK) cur = (cur + n) & 1;
+        } else {
+            for (int k = 0; k < n && e == cudaSuccess; ++k) e = issue_iteration(h, mode, sched, cur, count);
+        }
         cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
         if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e, "O(mM) update capture"); }
         if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
@@ -345,6 +445,7 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
     }
     if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
     h->tc_ready = false;
+    h->p_ready = false;
     h->have_potential = true;
     h->recorded = false;
     clear_graphs(h);
@@ -573,6 +674,14 @@ bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
     h->cur = saved_cur;
     BP_CK(h, cudaMemcpyAsync(h->msg[h->cur], h->tune_buf, bpg_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
     if (host_best_ms) *host_best_ms = best / (float)n_iters;
+    return BP_OK;
+}
+
+bp_status bp_set_persistent(bp_handle h, int mode) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_persistent: NULL handle");
+    h->err.clear();
+    if (mode < -1 || mode > 1) return fail(h, BP_ERR_ARG, "bp_set_persistent: mode must be -1, 0 or 1");
+    h->persistent = mode;
     return BP_OK;
 }
 

@@ -21,6 +21,8 @@ struct BatchMrf {
     int32_t ebar;
 };
 
+// A run of `count` consecutive slots of one MRF: nodes for a synchronous
+// iteration, half-step slots (see slot_node) for the red-black schedule.
 struct BatchItem {
     int mrf;
     int node0;
@@ -32,7 +34,8 @@ struct BatchArgs {
     const BatchItem *items;
     int n_items;
     int n_iters;
-    int start_buf;              // iteration t reads msg[(start_buf + t) & 1]
+    int start_buf;              // synchronous: iteration t reads msg[(start_buf + t) & 1]
+    int redblack;               // 1: two in-place half-steps per iteration on msg[start_buf]
     unsigned *bar_count;        // grid barrier: arrivals, generation
     unsigned *bar_gen;
     int extra_arrivals;         // 0; > 0 makes the barrier wait for blocks that never come

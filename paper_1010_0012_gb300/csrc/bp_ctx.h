@@ -13,9 +13,10 @@
 #include "bp_internal.h"
 
 struct GraphKey {
-    int n, mode, sched, cur, L, C, blocks;
+    int n, mode, sched, cur, L, C, blocks, persist;
     bool operator<(const GraphKey &o) const {
-        return std::tie(n, mode, sched, cur, L, C, blocks) < std::tie(o.n, o.mode, o.sched, o.cur, o.L, o.C, o.blocks);
+        return std::tie(n, mode, sched, cur, L, C, blocks, persist) <
+               std::tie(o.n, o.mode, o.sched, o.cur, o.L, o.C, o.blocks, o.persist);
     }
 };
 
@@ -76,6 +77,15 @@ struct bp_ctx {
     void *dlogg_pad = nullptr;      // [H][W][Mp] accumulated dL/d log g
     void *d_red = nullptr;          // FP64 reduced parameter gradients
     int rec_every = 5;
+
+    // one persistent launch per bp_iterate call (small grids): a one-MRF
+    // descriptor and work items for the persistent kernel of the batch path
+    int persistent = -1;            // -1 automatic, 0 never, 1 always (when served)
+    void *p_mrf = nullptr;          // device BatchMrf
+    void *p_items[2] = {nullptr, nullptr};   // synchronous / red-black slot items
+    int p_nitems[2] = {0, 0};
+    void *p_bar = nullptr;          // grid-barrier words
+    bool p_ready = false;           // descriptor matches the current potential
 
     // tensor-core dense baseline
     void *tc_a = nullptr;           // packed h rows, bf16 [4*H*W][Mp]

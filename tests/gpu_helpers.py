@@ -32,13 +32,15 @@ def oracle_V_from_table(table, T, ebar, M):
 
 
 def run_gpu_sum(g32, table, T, fbar, iters, schedule="sync", planes0=None, layout=None, dense=None,
-                log=False):
+                log=False, persistent=None):
     B = bp()
     t = torch()
     H, W, M = g32.shape
     G = B.BPGrid(W, H, M, B.BP_F32)
     if layout is not None:
         B.bp_set_layout(G.h, *layout)
+    if persistent is not None:
+        B.bp_set_persistent(G.h, persistent)
     G.set_unary(t.from_numpy(np.ascontiguousarray(g32)).cuda())
     G.set_potential(table, T, fbar)
     G.reset()
@@ -56,13 +58,16 @@ def run_gpu_sum(g32, table, T, fbar, iters, schedule="sync", planes0=None, layou
     return out
 
 
-def run_gpu_min(E32, table, T, ebar, iters, schedule="sync", planes0=None, layout=None, dense=None):
+def run_gpu_min(E32, table, T, ebar, iters, schedule="sync", planes0=None, layout=None, dense=None,
+                persistent=None):
     B = bp()
     t = torch()
     H, W, M = E32.shape
     G = B.BPGrid(W, H, M, B.BP_I32)
     if layout is not None:
         B.bp_set_layout(G.h, *layout)
+    if persistent is not None:
+        B.bp_set_persistent(G.h, persistent)
     G.set_unary(t.from_numpy(np.ascontiguousarray(E32, dtype=np.int32)).cuda())
     G.set_potential(table, T, ebar)
     G.reset()
@@ -108,10 +113,10 @@ def check_sum_map(map_gpu, bel_gpu, bel64, gap=1e-4):
 
 
 def check_sum_case(g32, table, T, fbar, iters, schedule="sync", planes0=None, layout=None, dense=None,
-                   log=False, tol=REL_TOL):
+                   log=False, tol=REL_TOL, persistent=None):
     H, W, M = g32.shape
     F = oracle_F_from_table(table, T, fbar, M)
-    bel, mp, msgs = run_gpu_sum(g32, table, T, fbar, iters, schedule, planes0, layout, dense, log)
+    bel, mp, msgs = run_gpu_sum(g32, table, T, fbar, iters, schedule, planes0, layout, dense, log, persistent)
     p64, b64 = grid.grid_sum_product(g32.astype(np.float64), F, iters,
                                      "sync" if dense is not None else schedule, planes0=planes0)
     if log:
@@ -124,10 +129,11 @@ def check_sum_case(g32, table, T, fbar, iters, schedule="sync", planes0=None, la
     return e_b, e_m
 
 
-def check_min_case(E, table, T, ebar, iters, schedule="sync", planes0=None, layout=None, dense=None):
+def check_min_case(E, table, T, ebar, iters, schedule="sync", planes0=None, layout=None, dense=None,
+                   persistent=None):
     H, W, M = E.shape
     V = oracle_V_from_table(table, T, ebar, M)
-    bel, mp, msgs = run_gpu_min(E, table, T, ebar, iters, schedule, planes0, layout, dense)
+    bel, mp, msgs = run_gpu_min(E, table, T, ebar, iters, schedule, planes0, layout, dense, persistent)
     p64, b64 = grid.grid_min_sum(E.astype(np.int64), V, iters, "sync" if dense is not None else schedule,
                                  planes0=planes0)
     src, dst, side, rr, cc = grid.grid_edges(W, H)

@@ -190,3 +190,41 @@ def test_mode_dtype_mismatch_is_an_argument_error():
         G.iterate(1, bp.BP_MAX)
     assert ei.value.status == bp.BP_ERR_ARG
     G.close()
+
+
+# ------------------------------------------- per-launch vs persistent issue --
+
+@pytest.mark.parametrize("persistent", [0, 1])
+@pytest.mark.parametrize("M,T", [(16, 2), (33, 3), (64, 8), (128, 4), (256, 5)])
+@pytest.mark.parametrize("schedule", ["sync", "redblack"])
+def test_both_issue_forms_match_the_oracle(persistent, M, T, schedule):
+    """The same iterations issued one launch per (half-)iteration, or as one
+    persistent launch with grid barriers between them."""
+    cfg = wl.small_config("p", 29, 17, M, T, alpha=0.8, structure="planar", seed=M * 7 + T)
+    st, g, E = H.stereo_inputs(cfg)
+    tab, fbar = wl.pair_table_f32(cfg.alpha, T)
+    H.check_sum_case(g, tab, T, fbar, 7, schedule, persistent=persistent)
+    tabi, ebar = wl.pair_table_i32(cfg.alpha, T)
+    H.check_min_case(E, tabi, T, ebar, 7, schedule, persistent=persistent)
+
+
+def test_persistent_issue_is_one_launch_per_call():
+    import torch
+    from paper_1010_0012_gb300 import bp
+    cfg = wl.CONFIGS["grid384x288_m16"]
+    st, g, E = H.stereo_inputs(cfg)
+    G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_I32)
+    G.set_unary(torch.from_numpy(E).cuda())
+    tabi, ebar = wl.pair_table_i32(cfg.alpha, cfg.T)
+    G.set_potential(tabi, cfg.T, ebar)
+    G.reset()
+    G.iterate(0, bp.BP_MAX)
+    n0 = G.launches
+    G.iterate(50, bp.BP_MAX, "redblack")
+    assert G.launches - n0 == 1
+    bp.bp_set_persistent(G.h, 0)
+    n1 = G.launches
+    G.iterate(50, bp.BP_MAX, "redblack")
+    assert G.launches - n1 == 100
+    G.sync()
+    G.close()
