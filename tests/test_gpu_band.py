@@ -148,8 +148,8 @@ def test_every_layout_agrees(M, T):
     for L, C in sorted(layouts):
         if L * 4 * C != Mp:
             continue
-        H.check_sum_case(g, tab, T, fbar, 3, "sync", layout=(L, C))
-        H.check_min_case(E, tabi, T, ebar, 3, "sync", layout=(L, C))
+        H.check_sum_case(g, tab, T, fbar, 3, "sync", layout=(L, C), persistent=0)
+        H.check_min_case(E, tabi, T, ebar, 3, "sync", layout=(L, C), persistent=0)
 
 
 # ------------------------------------------------------------- dense baselines --
