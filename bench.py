@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-baselines", action="store_true", help="skip the O(M^2) baselines")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--persistent", type=int, default=-1, choices=[-1, 0, 1],
+                    help="issue form of single-grid iterations (see bp_set_persistent)")
     ap.add_argument("--rows", type=int, default=0,
                     help="use only this many image rows (smaller case for profiling)")
     return ap.parse_args()
@@ -386,6 +388,7 @@ def run_grid_workload(args, name):
         u = torch.from_numpy(un).cuda()
         torch.cuda.synchronize()
         G = bp.BPGrid(cfg.W, cfg.H, cfg.M, dtype, stream=stream)
+        bp.bp_set_persistent(G.h, args.persistent)
         G.set_unary(u)
         G.set_potential(tabfb[0], cfg.T, tabfb[1])
 

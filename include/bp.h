@@ -234,8 +234,9 @@ void bp_batch_destroy(bp_batch b);
  * 1: ONE persistent cooperative launch for the whole call, with a bounded grid
  *    barrier between iterations (half-steps), where served (16 < Mp <= 256
  *    after padding, T <= 8); otherwise as 0;
- * -1 (default): 1 when one iteration moves under 96 MB (launch latency, not
- *    bandwidth, bounds such grids), else 0.  Results are identical. */
+ * -1 (default): the faster form as measured on GB300, currently 0 at every
+ *    size (CUDA-graph replay of per-iteration launches beats the persistent
+ *    kernel's grid barrier even on 32 x 32 grids).  Results are identical. */
 bp_status bp_set_persistent(bp_handle h, int mode);
 
 /* Number of kernel launches the library issued on this handle so far. */

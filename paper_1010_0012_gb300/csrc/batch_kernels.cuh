@@ -26,33 +26,42 @@ __device__ __forceinline__ unsigned long long batch_timer() {
 }
 
 // Sense-reversing grid barrier over `expected` arrivals.  Returns false (in
-// every thread of the block) if the wait ran out.
+// every thread of the block) if the wait ran out.  Thread 0 of each block
+// publishes the block's writes (bar.sync then a gpu-scope acq_rel fence),
+// arrives on the counter, and the last arrival bumps the generation word the
+// others poll.
 __device__ __forceinline__ bool batch_grid_barrier(unsigned *count, unsigned *gen, unsigned expected,
                                                    unsigned long long limit_ns, int *status) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        volatile unsigned *vgen = gen;
-        const unsigned g = *vgen;
-        __threadfence();
+        unsigned g;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         const unsigned arrived = atomicAdd(count, 1u) + 1u;
         if (arrived == expected) {
             atomicExch(count, 0u);
-            __threadfence();
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             atomicAdd(gen, 1u);
         } else {
-            const unsigned long long t0 = batch_timer();
-            while (*vgen == g) {
-                if (batch_timer() - t0 > limit_ns) {
-                    ok = 0;
-                    atomicExch(status, 201);
-                    break;
+            unsigned long long t0 = 0;
+            for (unsigned spins = 0;; ++spins) {
+                unsigned cur;
+                asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+                if (cur != g) break;
+                if ((spins & 1023u) == 0) {
+                    const unsigned long long now = batch_timer();
+                    if (spins == 0) t0 = now;
+                    else if (now - t0 > limit_ns) {
+                        ok = 0;
+                        atomicExch(status, 201);
+                        break;
+                    }
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
     }
     __syncthreads();
     return ok != 0;
@@ -143,7 +152,6 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
             batch_dispatch<FAM, MIN>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
         }
         if (step + 1 < total) {
-            __threadfence();
             if (!batch_grid_barrier(a.bar_count, a.bar_gen, gridDim.x + a.extra_arrivals, a.limit_ns, a.status))
                 return;
         }

@@ -160,18 +160,17 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
 
 // ---- one persistent launch for a whole bp_iterate call -----------------------
 // Served for the linear sum-product and min-sum updates with 16 <= Mp <= 256
-// and T <= 8 (the label classes of the persistent kernel).  Automatic mode
-// takes it when one iteration moves less than 96 MB, where launch latency
-// rather than HBM bandwidth bounds the per-launch form.
+// and T <= 8 (the label classes of the persistent kernel), on request.  The
+// automatic choice is the per-launch form: on GB300, graph-replayed kernel
+// boundaries (2.7 us per iteration at 32x32, 6.1 us per red-black half-step
+// at 384x288) measured faster than this kernel's grid barrier and per-step
+// descriptor reads (5.0 us and 10.2 us).
 static bool persistent_served(const bp_ctx *h, int mode) {
     return h->fast && !(mode & BP_LOG) && h->Mp >= 16 && h->Mp <= 256 && h->Teff <= kTMaxFast;
 }
 
 static bool use_persistent(const bp_ctx *h, int mode) {
-    if (h->persistent == 0 || !persistent_served(h, mode)) return false;
-    if (h->persistent == 1) return true;
-    const double bytes = ((double)h->W * h->H * h->M + 8.0 * h->W * h->H * h->M) * 4.0;
-    return bytes < 96e6;
+    return h->persistent == 1 && persistent_served(h, mode);
 }
 
 static bp_status persistent_setup(bp_ctx *h) {
