@@ -98,6 +98,19 @@ bp_status bp_set_unary_log(bp_handle h, const float *dev_logg);
  * 0 <= T; T >= M - 1 makes the band cover every label pair. */
 bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fbar);
 
+/* General sparse compatibility (Sec. 4: Nbd(x_j) of any shape; Sec. 7:
+ * robust potentials that are not a function of x_i - x_j).  For each receiver
+ * label x_j, host_cols[host_rowptr[x_j] .. host_rowptr[x_j+1]) lists the
+ * compatible sender labels x_i (distinct, in [0, M)) and host_vals holds
+ * f(x_i, x_j) (float32) or E(x_i, x_j) (int32) for them; every other pair has
+ * fbar (Ebar).  host_rowptr has M+1 entries, rowptr[0] = 0.  One message then
+ * costs O(nnz) with nnz = rowptr[M] (O(mM) for m pairs per label).  Replaces
+ * any band potential; BP_ERR_POTENTIAL in max mode if some E > Ebar;
+ * BP_ERR_ARG if the pattern does not fit the kernel's shared memory (about
+ * 25,000 pairs at M = 128).  Log mode and bp_backward need a band potential. */
+bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
+                                  const void *host_vals, double fbar);
+
 /* Uniform initial messages: 1/M (sum), 0 (min-sum), log(1/M) (log mode). */
 bp_status bp_reset_messages(bp_handle h);
 

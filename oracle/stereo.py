@@ -56,3 +56,14 @@ def matching_cost(left: np.ndarray, right: np.ndarray, M: int, Tu: int) -> np.nd
 def unary_potential(left, right, M, beta, Tu) -> np.ndarray:
     """g[r, c, x] = exp(-beta * cost[r, c, x]), float64."""
     return np.exp(-beta * matching_cost(left, right, M, Tu).astype(np.float64))
+
+
+def sparse_compatibility_matrix(rowptr, cols, vals, fbar, M, dtype=np.float64) -> np.ndarray:
+    """A sparse-compatibility potential given per receiver label x_j by the
+    list of compatible sender labels x_i and their values (Sec. 4): F[x_i, x_j]
+    is that value when x_i is listed for x_j, fbar otherwise."""
+    F = np.full((M, M), fbar, dtype=dtype)
+    for xj in range(M):
+        for p in range(rowptr[xj], rowptr[xj + 1]):
+            F[cols[p], xj] = vals[p]
+    return F

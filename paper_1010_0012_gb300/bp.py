@@ -43,6 +43,7 @@ def _load():
         "bp_set_unary": ([P, P], I),
         "bp_set_unary_log": ([P, P], I),
         "bp_set_potential": ([P, P, I, D], I),
+        "bp_set_potential_sparse": ([P, P, P, P, D], I),
         "bp_reset_messages": ([P], I),
         "bp_iterate": ([P, I, I, I], I),
         "bp_iterate_dense": ([P, I, I], I),
@@ -139,6 +140,20 @@ def bp_set_potential(h, table, T: int, fbar: float, dtype):
     if arr.size != 2 * T + 1:
         raise ValueError("table must hold 2T + 1 values")
     _check(h, _lib.bp_set_potential(h, arr.ctypes.data_as(ctypes.c_void_p), int(T), float(fbar)))
+
+
+def bp_set_potential_sparse(h, rowptr, cols, vals, fbar: float, dtype):
+    """CSR over receiver labels: cols[rowptr[xj]:rowptr[xj+1]] are the
+    compatible sender labels of xj, vals their f (or E)."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    cl = np.ascontiguousarray(cols, dtype=np.int32)
+    vl = np.ascontiguousarray(vals, dtype=np.float32 if dtype == BP_F32 else np.int32)
+    if cl.size != vl.size or rp[-1] != cl.size:
+        raise ValueError("rowptr[-1] must equal len(cols) == len(vals)")
+    _check(h, _lib.bp_set_potential_sparse(h, rp.ctypes.data_as(ctypes.c_void_p),
+                                           cl.ctypes.data_as(ctypes.c_void_p) if cl.size else None,
+                                           vl.ctypes.data_as(ctypes.c_void_p), float(fbar)))
 
 
 def bp_reset_messages(h):

@@ -16,6 +16,7 @@
 #include "bp_batch_internal.h"
 #include "bp_internal.h"
 #include "bp_ctx.h"
+#include "bp_sparse.h"
 
 namespace bpg {
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
@@ -123,6 +124,24 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
         void *in = h->msg[cur];
         void *out = sched == BP_REDBLACK ? h->msg[cur] : h->msg[cur ^ 1];
         cudaError_t e;
+        if (h->sparse) {
+            if (is_log) return cudaErrorNotSupported;
+            const int nnz = (int)h->sp_cols.size();
+            if (h->dtype == BP_I32) {
+                SparseArgsI a{(const int32_t *)h->unary, (const int32_t *)in, (int32_t *)out, h->dims, parity,
+                              (const int32_t *)h->d_sp_rowptr, (const int32_t *)h->d_sp_cols,
+                              (const int32_t *)h->d_sp_w, nnz, h->ebar};
+                e = launch_sparse_min(a, h->stream);
+            } else {
+                SparseArgsF a{(const float *)h->unary, (const float *)in, (float *)out, h->dims, parity,
+                              (const int32_t *)h->d_sp_rowptr, (const int32_t *)h->d_sp_cols,
+                              (const float *)h->d_sp_w, nnz, h->fbarf};
+                e = launch_sparse_sum(a, h->stream);
+            }
+            if (e != cudaSuccess) return e;
+            ++count;
+            continue;
+        }
         if (h->dtype == BP_I32) {
             if (h->fast) {
                 BandArgsI a{};
@@ -166,7 +185,7 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
 // at 384x288) measured faster than this kernel's grid barrier and per-step
 // descriptor reads (5.0 us and 10.2 us).
 static bool persistent_served(const bp_ctx *h, int mode) {
-    return h->fast && !(mode & BP_LOG) && h->Mp >= 16 && h->Mp <= 256 && h->Teff <= kTMaxFast;
+    return h->fast && !h->sparse && !(mode & BP_LOG) && h->Mp >= 16 && h->Mp <= 256 && h->Teff <= kTMaxFast;
 }
 
 static bool use_persistent(const bp_ctx *h, int mode) {
@@ -348,7 +367,7 @@ void bp_destroy(bp_handle h) {
     clear_graphs(h);
     bpg_free_extras(h);
     void *bufs[] = {h->unary, h->log_unary, h->msg[0], h->msg[1], h->d_wf, h->d_wi, h->d_dense, h->d_status,
-                    h->tune_buf};
+                    h->tune_buf, h->d_sp_rowptr, h->d_sp_cols, h->d_sp_w};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -423,6 +442,7 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
         h->wi.resize(2 * Teff + 1);
         for (int d = -Teff; d <= Teff; ++d) h->wi[d + Teff] = tab[d + T];
     }
+    h->sparse = false;
     h->T = T;
     h->Teff = Teff;
     h->fbar = fbar;
@@ -443,6 +463,85 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
         BP_CK(h, cudaStreamSynchronize(h->stream));
     }
     if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
+    h->tc_ready = false;
+    h->p_ready = false;
+    h->have_potential = true;
+    h->recorded = false;
+    clear_graphs(h);
+    return BP_OK;
+}
+
+bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
+                                  const void *host_vals, double fbar) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_potential_sparse: NULL handle");
+    h->err.clear();
+    if (!host_rowptr || !host_vals || (!host_cols && host_rowptr[h->M] != 0))
+        return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: NULL argument");
+    if (!std::isfinite(fbar) || fbar < 0) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: fbar must be >= 0");
+    if (host_rowptr[0] != 0) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: rowptr[0] must be 0");
+    for (int x = 0; x < h->M; ++x)
+        if (host_rowptr[x + 1] < host_rowptr[x]) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: rowptr decreases");
+    const int nnz = host_rowptr[h->M];
+    if (sparse_smem_bytes(h->M, h->Mp, nnz) > 220 * 1024)
+        return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: too many compatible pairs for shared memory");
+    std::vector<char> seen(h->M, 0);
+    for (int xj = 0; xj < h->M; ++xj) {
+        for (int p = host_rowptr[xj]; p < host_rowptr[xj + 1]; ++p) {
+            const int xi = host_cols[p];
+            if (xi < 0 || xi >= h->M) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: column out of range");
+            if (seen[xi]) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: repeated column in a row");
+            seen[xi] = 1;
+        }
+        for (int p = host_rowptr[xj]; p < host_rowptr[xj + 1]; ++p) seen[host_cols[p]] = 0;
+    }
+    std::vector<float> wf;
+    std::vector<int32_t> wi;
+    if (h->dtype == BP_F32) {
+        const float *v = (const float *)host_vals;
+        for (int p = 0; p < nnz; ++p)
+            if (!std::isfinite(v[p]) || v[p] < 0)
+                return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: values must be finite and >= 0");
+        h->sp_valf.assign(v, v + nnz);
+        h->fbarf = (float)fbar;
+        for (int p = 0; p < nnz; ++p) wf.push_back((float)((double)v[p] - (double)h->fbarf));
+    } else {
+        if (fbar != std::floor(fbar) || fbar >= (double)(1 << 26))
+            return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: Ebar must be an integer in [0, 2^26)");
+        const int32_t *v = (const int32_t *)host_vals;
+        for (int p = 0; p < nnz; ++p) {
+            if (v[p] < 0 || v[p] >= (1 << 26)) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: energies out of range");
+            if (v[p] > (int32_t)fbar)
+                return fail(h, BP_ERR_POTENTIAL,
+                            "bp_set_potential_sparse: E > Ebar; Eq. 11 is exact only when f >= fbar (Sec. 5)");
+        }
+        h->sp_vali.assign(v, v + nnz);
+        h->ebar = (int32_t)fbar;
+        wi.assign(v, v + nnz);
+    }
+    h->sp_rowptr.assign(host_rowptr, host_rowptr + h->M + 1);
+    h->sp_cols.assign(host_cols, host_cols + nnz);
+    void *bufs[] = {h->d_sp_rowptr, h->d_sp_cols, h->d_sp_w};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    h->d_sp_rowptr = h->d_sp_cols = h->d_sp_w = nullptr;
+    const size_t cb = (size_t)(nnz > 0 ? nnz : 1) * 4;
+    if (bp_status st = ensure_buffer(h, &h->d_sp_rowptr, (size_t)(h->M + 1) * 4, "sparse rowptr")) return st;
+    if (bp_status st = ensure_buffer(h, &h->d_sp_cols, cb, "sparse columns")) return st;
+    if (bp_status st = ensure_buffer(h, &h->d_sp_w, cb, "sparse values")) return st;
+    BP_CK(h, cudaMemcpyAsync(h->d_sp_rowptr, h->sp_rowptr.data(), (size_t)(h->M + 1) * 4, cudaMemcpyHostToDevice,
+                             h->stream));
+    if (nnz > 0) {
+        BP_CK(h, cudaMemcpyAsync(h->d_sp_cols, h->sp_cols.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, h->stream));
+        BP_CK(h, cudaMemcpyAsync(h->d_sp_w, h->dtype == BP_F32 ? (const void *)wf.data() : (const void *)wi.data(),
+                                 (size_t)nnz * 4, cudaMemcpyHostToDevice, h->stream));
+    }
+    BP_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
+    h->sparse = true;
+    h->fast = false;
+    h->fbar = fbar;
+    h->T = 0;
+    h->Teff = 0;
     h->tc_ready = false;
     h->p_ready = false;
     h->have_potential = true;
@@ -495,8 +594,8 @@ bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule) {
     if (rec && schedule != BP_SYNC) return fail(h, BP_ERR_ARG, "bp_iterate: BP_RECORD needs BP_SYNC");
     if (!h->have_unary || !h->have_potential)
         return fail(h, BP_ERR_STATE, "bp_iterate: set the unary and the potential first");
-    if (is_log && !h->fast)
-        return fail(h, BP_ERR_UNSUPPORTED, "bp_iterate: log mode needs T <= 8 and M <= 512");
+    if (is_log && (!h->fast || h->sparse))
+        return fail(h, BP_ERR_UNSUPPORTED, "bp_iterate: log mode needs a band potential with T <= 8 and M <= 512");
     if (bp_status st = bpg_check_device(h)) return st;
     if (is_log) {
         if (bp_status st = ensure_log_unary(h)) return st;
@@ -530,10 +629,8 @@ bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind) {
         if (h->dtype == BP_F32) F.resize((size_t)h->M * h->M); else V.resize((size_t)h->M * h->M);
         for (int xi = 0; xi < h->M; ++xi)
             for (int xj = 0; xj < h->M; ++xj) {
-                const int d = xi - xj;
-                const bool in_band = d >= -h->T && d <= h->T;
-                if (h->dtype == BP_F32) F[(size_t)xi * h->M + xj] = in_band ? h->tablef[d + h->T] : h->fbarf;
-                else V[(size_t)xi * h->M + xj] = in_band ? h->tablei[d + h->T] : h->ebar;
+                if (h->dtype == BP_F32) F[(size_t)xi * h->M + xj] = bpg_pair_value_f(h, xi, xj);
+                else V[(size_t)xi * h->M + xj] = bpg_pair_value_i(h, xi, xj);
             }
         if (bp_status st = ensure_buffer(h, &h->d_dense, bytes, "dense table")) return st;
         BP_CK(h, cudaMemcpyAsync(h->d_dense, h->dtype == BP_F32 ? (const void *)F.data() : (const void *)V.data(),
@@ -630,6 +727,7 @@ bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
     h->err.clear();
     if (n_iters < 1) return fail(h, BP_ERR_ARG, "bp_autotune: n_iters < 1");
     if (!h->have_unary || !h->have_potential) return fail(h, BP_ERR_STATE, "bp_autotune: set unary and potential first");
+    if (h->sparse) return fail(h, BP_ERR_UNSUPPORTED, "bp_autotune: tunes the band kernels only");
     const bool is_log = (mode & BP_LOG) != 0;
     if (bp_status st = bpg_check_device(h)) return st;
     if (is_log)
@@ -693,6 +791,28 @@ bp_status bp_set_checkpoint_interval(bp_handle h, int every) {
 }
 
 }  // extern "C"
+
+// Value of the pairwise potential at (x_i, x_j) as the handle holds it: the
+// band table or the sparse list, fbar (Ebar) elsewhere.
+float bpg_pair_value_f(const bp_ctx *h, int xi, int xj) {
+    if (h->sparse) {
+        for (int p = h->sp_rowptr[xj]; p < h->sp_rowptr[xj + 1]; ++p)
+            if (h->sp_cols[p] == xi) return h->sp_valf[p];
+        return h->fbarf;
+    }
+    const int d = xi - xj;
+    return (d >= -h->T && d <= h->T) ? h->tablef[d + h->T] : h->fbarf;
+}
+
+int32_t bpg_pair_value_i(const bp_ctx *h, int xi, int xj) {
+    if (h->sparse) {
+        for (int p = h->sp_rowptr[xj]; p < h->sp_rowptr[xj + 1]; ++p)
+            if (h->sp_cols[p] == xi) return h->sp_vali[p];
+        return h->ebar;
+    }
+    const int d = xi - xj;
+    return (d >= -h->T && d <= h->T) ? h->tablei[d + h->T] : h->ebar;
+}
 
 // Shared with bp_backward.cu / dense_tc.cu.
 bp_status bpg_fail(bp_ctx *h, bp_status st, const std::string &msg) { return fail(h, st, msg); }

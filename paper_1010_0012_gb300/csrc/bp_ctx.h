@@ -53,6 +53,13 @@ struct bp_ctx {
     int32_t *d_wi = nullptr;
     void *d_dense = nullptr;        // device M x M table for the CUDA-core dense baseline
 
+    // general sparse compatibility (bp_set_potential_sparse)
+    bool sparse = false;
+    std::vector<int32_t> sp_rowptr, sp_cols;
+    std::vector<float> sp_valf;      // f(x_i, x_j)
+    std::vector<int32_t> sp_vali;    // E(x_i, x_j)
+    void *d_sp_rowptr = nullptr, *d_sp_cols = nullptr, *d_sp_w = nullptr;
+
     bpg::Layout layout{32, 1};
     bool fast = false;              // register/shuffle kernels serve (M, T)
     int blocks_override = 0;
@@ -104,6 +111,8 @@ size_t bpg_state_bytes(const bp_ctx *h);
 cudaError_t bpg_issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int &count);
 
 bp_status bpg_record_forward(bp_ctx *h, int n_iters);   // bp_backward.cu
+float bpg_pair_value_f(const bp_ctx *h, int xi, int xj);   // bp_api.cu
+int32_t bpg_pair_value_i(const bp_ctx *h, int xi, int xj);
 void bpg_free_extras(bp_ctx *h);                         // bp_backward.cu
 bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters);  // dense_tc.cu
 bp_status bpg_dense_tc_iterate_kind(bp_ctx *h, int n_iters, bool fused);

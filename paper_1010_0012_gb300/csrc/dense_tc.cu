@@ -715,10 +715,7 @@ bp_status bpg_dense_tc_iterate_kind(bp_ctx *h, int n_iters, bool fused) {
         // B[x_j][x_i] = f(x_i, x_j) (F transposed: K = x_i contiguous), zero outside M
         std::vector<float> Bt((size_t)Mp * Mp, 0.f);
         for (int xj = 0; xj < h->M; ++xj)
-            for (int xi = 0; xi < h->M; ++xi) {
-                const int d = xi - xj;
-                Bt[(size_t)xj * Mp + xi] = (d >= -h->T && d <= h->T) ? h->tablef[d + h->T] : h->fbarf;
-            }
+            for (int xi = 0; xi < h->M; ++xi) Bt[(size_t)xj * Mp + xi] = bpg_pair_value_f(h, xi, xj);
         cudaError_t e = cudaMemcpyAsync(h->tc_z, Bt.data(), Bt.size() * 4, cudaMemcpyHostToDevice, h->stream);
         if (e != cudaSuccess) return bpg_cuda_fail(h, e, "tensor-core B upload");
         to_bf16_kernel<<<64, 256, 0, h->stream>>>((const float *)h->tc_z, (__nv_bfloat16 *)h->tc_b, Mp * Mp);

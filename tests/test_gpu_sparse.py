@@ -1,0 +1,119 @@
+"""General sparse compatibility (Sec. 4, Sec. 7): arbitrary per-label lists of
+compatible states, including potentials that are not a function of
+x_i - x_j, against the dense oracle built from the same lists."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import grid, stereo
+from paper_1010_0012_gb300 import workload as wl
+from tests import gpu_helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def random_pattern(M, max_per_row, rng, integer=False, ebar=40):
+    rowptr, cols, vals = [0], [], []
+    for xj in range(M):
+        k = int(rng.integers(0, max_per_row + 1))
+        xs = rng.choice(M, size=k, replace=False)
+        cols.extend(int(x) for x in xs)
+        if integer:
+            vals.extend(int(v) for v in rng.integers(0, ebar + 1, k))
+        else:
+            vals.extend(float(v) for v in rng.uniform(0.05, 2.0, k))
+        rowptr.append(len(cols))
+    return (np.array(rowptr, np.int32), np.array(cols, np.int32),
+            np.array(vals, np.int32 if integer else np.float32))
+
+
+def _run(M, dtype, planes0, unary, pattern, fbar, iters, schedule):
+    import torch
+    from paper_1010_0012_gb300 import bp
+    Hh, W, _ = unary.shape
+    G = bp.BPGrid(W, Hh, M, dtype)
+    G.set_unary(torch.from_numpy(unary).cuda())
+    bp.bp_set_potential_sparse(G.h, *pattern, fbar, dtype)
+    G.reset()
+    if planes0 is not None:
+        G.set_messages(torch.from_numpy(planes0).cuda())
+    G.iterate(iters, bp.BP_SUM if dtype == bp.BP_F32 else bp.BP_MAX, schedule)
+    bel, mp = G.beliefs()
+    pl = G.get_messages()
+    G.sync()
+    out = bel.cpu().numpy(), mp.cpu().numpy(), pl.cpu().numpy()
+    G.close()
+    return out
+
+
+@pytest.mark.parametrize("M,k", [(16, 5), (37, 9), (128, 9), (256, 4)])
+@pytest.mark.parametrize("schedule", ["sync", "redblack"])
+def test_sparse_sum_matches_oracle(M, k, schedule):
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(M + k)
+    W, Hh = 11, 7
+    g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
+    pat = random_pattern(M, k, rng)
+    fbar = 0.12
+    p0 = H.random_planes_sum(W, Hh, M, rng)
+    bel, mp, pl = _run(M, bp.BP_F32, p0, g, pat, fbar, 3, schedule)
+    F = stereo.sparse_compatibility_matrix(*[x.astype(np.float64) if i == 2 else x for i, x in enumerate(pat)],
+                                           fbar, M)
+    p64, b64 = grid.grid_sum_product(g.astype(np.float64), F, 3, schedule, planes0=p0)
+    assert H.node_rel_err(bel, b64) <= H.REL_TOL
+    assert H.message_rel_err(pl, p64, W, Hh) <= H.REL_TOL
+
+
+@pytest.mark.parametrize("M,k", [(16, 5), (64, 7), (200, 6)])
+@pytest.mark.parametrize("schedule", ["sync", "redblack"])
+def test_sparse_min_matches_oracle_bit_exact(M, k, schedule):
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(10 * M + k)
+    W, Hh = 9, 8
+    E = rng.integers(0, 30, (Hh, W, M)).astype(np.int32)
+    ebar = 40
+    pat = random_pattern(M, k, rng, integer=True, ebar=ebar)
+    p0 = H.random_planes_min(W, Hh, M, rng)
+    bel, mp, pl = _run(M, bp.BP_I32, p0, E, pat, ebar, 4, schedule)
+    V = stereo.sparse_compatibility_matrix(pat[0], pat[1], pat[2].astype(np.int64), ebar, M, dtype=np.int64)
+    p64, b64 = grid.grid_min_sum(E.astype(np.int64), V, 4, schedule, planes0=p0)
+    src, dst, side, rr, cc = grid.grid_edges(W, Hh)
+    np.testing.assert_array_equal(pl.astype(np.int64)[side, rr, cc], p64[side, rr, cc])
+    np.testing.assert_array_equal(bel.astype(np.int64), b64)
+    np.testing.assert_array_equal(mp, oracle.map_labels(b64, maximise=False))
+
+
+def test_band_written_as_lists_equals_the_band_kernel():
+    """The truncated potential as a sparse pattern (|x_i - x_j| <= T) gives the
+    band kernel's messages (integer: bit for bit)."""
+    from paper_1010_0012_gb300 import bp
+    cfg = wl.small_config("sb", 21, 13, 64, 3, alpha=0.7, structure="planar", seed=2)
+    st, g, E = H.stereo_inputs(cfg)
+    tabi, ebar = wl.pair_table_i32(cfg.alpha, cfg.T)
+    rowptr, cols, vals = [0], [], []
+    for xj in range(cfg.M):
+        for d in range(-cfg.T, cfg.T + 1):
+            if 0 <= xj + d < cfg.M:
+                cols.append(xj + d)
+                vals.append(int(tabi[d + cfg.T]))
+        rowptr.append(len(cols))
+    pat = (np.array(rowptr, np.int32), np.array(cols, np.int32), np.array(vals, np.int32))
+    bel_s, _, pl_s = _run(cfg.M, bp.BP_I32, None, E, pat, ebar, 6, "sync")
+    bel_b, _, pl_b = H.run_gpu_min(E, tabi, cfg.T, ebar, 6, "sync")
+    np.testing.assert_array_equal(bel_s, bel_b)
+    src, dst, side, rr, cc = grid.grid_edges(cfg.W, cfg.H)
+    np.testing.assert_array_equal(pl_s[side, rr, cc], pl_b[side, rr, cc])
+
+
+def test_sparse_max_mode_rejects_energy_above_ebar():
+    import torch
+    from paper_1010_0012_gb300 import bp
+    G = bp.BPGrid(4, 4, 8, bp.BP_I32)
+    rowptr = np.array([0, 1, 1, 1, 1, 1, 1, 1, 1], np.int32)
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_set_potential_sparse(G.h, rowptr, np.array([3], np.int32), np.array([9], np.int32), 5, bp.BP_I32)
+    assert ei.value.status == bp.BP_ERR_POTENTIAL
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_set_potential_sparse(G.h, rowptr, np.array([8], np.int32), np.array([1], np.int32), 5, bp.BP_I32)
+    assert ei.value.status == bp.BP_ERR_ARG
+    G.close()

@@ -229,3 +229,19 @@ def test_sampled_updates_agree_with_full_iteration():
     for (r, c, t), m in zip(samples, got):
         dr, dc = grid.SIDE_OFFSETS[t]
         np.testing.assert_allclose(m, p1[grid.OPPOSITE[t], r + dr, c + dc], rtol=1e-14)
+
+
+def test_sparse_lists_of_a_band_give_the_band_matrix():
+    """A sparse-compatibility potential listing |x_i - x_j| <= T for every x_j
+    is the truncated band potential."""
+    M, T = 11, 2
+    band = np.array([0.3, 0.7, 1.0, 0.6, 0.2])
+    rowptr, cols, vals = [0], [], []
+    for xj in range(M):
+        for d in range(-T, T + 1):
+            if 0 <= xj + d < M:
+                cols.append(xj + d)
+                vals.append(band[d + T])
+        rowptr.append(len(cols))
+    np.testing.assert_array_equal(stereo.sparse_compatibility_matrix(rowptr, cols, vals, 0.05, M),
+                                  stereo.compatibility_matrix(band, T, 0.05, M))
