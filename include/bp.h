@@ -120,6 +120,17 @@ bp_status bp_reset_messages(bp_handle h);
  * normalised after each update (sum 1, or minimum 0 for min-sum). */
 bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule);
 
+/* Coarse-to-fine BP (the multi-scale scheme of [2], combined with the O(mM)
+ * update as Sec. 2 and Sec. 6 suggest).  Level l+1 has one node per 2 x 2 block
+ * of level l, unary = product of the block's g (sum of energies for min-sum),
+ * the handle's pairwise potential at every level.  host_iters[k] iterations run
+ * at level n_levels-1-k (coarsest first, host_iters[n_levels-1] on this grid);
+ * each finer level starts from the coarser level's final messages copied by
+ * direction (uniform where the coarse node has no neighbour on that side).
+ * mode BP_SUM or BP_MAX; either schedule.  Leaves this grid's messages as after
+ * bp_iterate.  The coarse levels are allocated on the first call. */
+bp_status bp_iterate_multiscale(bp_handle h, int n_levels, const int *host_iters, int mode, bp_schedule schedule);
+
 /* Run n_iters synchronous iterations of the dense O(M^2) update (Eq. 2 or
  * Eq. 9), the baseline the O(mM) update is measured against. */
 bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind);

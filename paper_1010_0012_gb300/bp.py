@@ -47,6 +47,7 @@ def _load():
         "bp_reset_messages": ([P], I),
         "bp_iterate": ([P, I, I, I], I),
         "bp_iterate_dense": ([P, I, I], I),
+        "bp_iterate_multiscale": ([P, I, P, I, I], I),
         "bp_beliefs": ([P, P, P], I),
         "bp_get_messages": ([P, P], I),
         "bp_set_messages": ([P, P], I),
@@ -162,6 +163,14 @@ def bp_reset_messages(h):
 
 def bp_iterate(h, n_iters, mode=BP_SUM, schedule=BP_SYNC):
     _check(h, _lib.bp_iterate(h, int(n_iters), int(mode), int(schedule)))
+
+
+def bp_iterate_multiscale(h, iters, mode=BP_SUM, schedule=BP_SYNC):
+    """iters: iteration counts per level, coarsest first (last = this grid)."""
+    import numpy as np
+    it = np.ascontiguousarray(iters, dtype=np.int32)
+    _check(h, _lib.bp_iterate_multiscale(h, int(it.size), it.ctypes.data_as(ctypes.c_void_p), int(mode),
+                                         int(SCHEDULES.get(schedule, schedule))))
 
 
 def bp_iterate_dense(h, n_iters, kind=BP_DENSE_CUDA_CORE):

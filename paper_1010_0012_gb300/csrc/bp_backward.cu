@@ -18,6 +18,7 @@ using namespace bpg;
 
 void bpg_free_extras(bp_ctx *h) {
     bpg_free_tc(h);
+    bpg_free_levels(h);
     for (void *p : h->ckpts)
         if (p) cudaFree(p);
     h->ckpts.clear();

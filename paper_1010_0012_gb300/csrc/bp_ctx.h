@@ -94,6 +94,9 @@ struct bp_ctx {
     void *p_bar = nullptr;          // grid-barrier words
     bool p_ready = false;           // descriptor matches the current potential
 
+    // coarse levels of bp_iterate_multiscale (child handles, level 1..L-1)
+    std::vector<bp_ctx *> levels;
+
     // tensor-core dense baseline
     void *tc_a = nullptr;           // packed h rows, bf16 [4*H*W][Mp]
     void *tc_b = nullptr;           // F^T, bf16 [Mp][Mp]
@@ -117,6 +120,7 @@ void bpg_free_extras(bp_ctx *h);                         // bp_backward.cu
 bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters);  // dense_tc.cu
 bp_status bpg_dense_tc_iterate_kind(bp_ctx *h, int n_iters, bool fused);
 void bpg_free_tc(bp_ctx *h);                             // dense_tc.cu
+void bpg_free_levels(bp_ctx *h);                         // bp_multiscale.cu
 
 namespace bpg {
 cudaError_t launch_domain_convert(float *planes, long long rows, int M, int Mp, int to_log, cudaStream_t s);
