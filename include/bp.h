@@ -122,7 +122,9 @@ bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule);
 
 /* Coarse-to-fine BP (the multi-scale scheme of [2], combined with the O(mM)
  * update as Sec. 2 and Sec. 6 suggest).  Level l+1 has one node per 2 x 2 block
- * of level l, unary = product of the block's g (sum of energies for min-sum),
+ * of level l, unary = product of the block's g scaled to maximum 1 per node
+ * (BP is unchanged by that scale; it keeps FP32 in range) or the sum of the
+ * block's energies for min-sum,
  * the handle's pairwise potential at every level.  host_iters[k] iterations run
  * at level n_levels-1-k (coarsest first, host_iters[n_levels-1] on this grid);
  * each finer level starts from the coarser level's final messages copied by
