@@ -10,6 +10,8 @@ finer level start as the final messages of the coarser one, copied by
 direction: the message into (r, c) from side s starts as the message into
 (r // 2, c // 2) from side s, or uniform where the coarse node has no
 neighbour on that side.  Then BP runs on that level, down to the given grid.
+Coarse unaries are kept scaled to maximum 1 per node (formed in logs); a
+per-node scale of g changes no message and no belief.
 """
 from __future__ import annotations
 
@@ -48,13 +50,24 @@ def upsample_messages(planes_c, H, W, fill):
     return out
 
 
+def coarsen_log(lu):
+    """Coarse log-unary: the block sum of log g (the log of the block product),
+    minus its maximum over labels -- the product scaled to maximum 1 per node,
+    which BP does not see and which keeps products of thousands of unaries
+    representable."""
+    s = coarsen(lu, np.sum)
+    return s - s.max(axis=-1, keepdims=True)
+
+
 def multiscale_sum_product(g, F, iters, schedule="sync"):
     """iters[k] iterations at level len(iters)-1-k (coarsest first).  Returns
     the finest planes and beliefs (float64)."""
     levels = len(iters)
     pyr = [np.asarray(g, dtype=np.float64)]
+    lu = np.log(pyr[0])
     for _ in range(levels - 1):
-        pyr.append(coarsen(pyr[-1], np.prod))
+        lu = coarsen_log(lu)
+        pyr.append(np.exp(lu))
     planes = None
     for k, lvl in enumerate(range(levels - 1, -1, -1)):
         u = pyr[lvl]

@@ -23,7 +23,7 @@ void bpg_free_extras(bp_ctx *h) {
         if (p) cudaFree(p);
     h->ckpts.clear();
     void *bufs[] = {h->seg_buf, h->adj[0], h->adj[1], h->dtab_partial, h->tc_a, h->tc_b, h->tc_z, h->dlogg_pad,
-                    h->d_red, h->p_mrf, h->p_items[0], h->p_items[1], h->p_bar};
+                    h->d_red, h->p_mrf, h->p_items[0], h->p_items[1], h->p_bar, h->ms_logu};
     for (void *p : bufs)
         if (p) cudaFree(p);
 }

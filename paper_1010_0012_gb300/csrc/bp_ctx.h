@@ -96,6 +96,7 @@ struct bp_ctx {
 
     // coarse levels of bp_iterate_multiscale (child handles, level 1..L-1)
     std::vector<bp_ctx *> levels;
+    void *ms_logu = nullptr;        // a level's log unary, scaled to maximum 0 (float)
 
     // tensor-core dense baseline
     void *tc_a = nullptr;           // packed h rows, bf16 [4*H*W][Mp]

@@ -2,8 +2,9 @@
 // O(mM) update (Sec. 2, Sec. 6).
 //
 // Level l+1 has one node per 2 x 2 block of level l; its unary is the product
-// of the block's unaries, scaled to maximum 1 per node (sum of energies for
-// min-sum); every level uses the handle's pairwise potential.  BP runs on the coarsest level from uniform
+// of the block's unaries, scaled to maximum 1 per node and formed in logs
+// (sum of energies for min-sum); every level uses the handle's pairwise
+// potential.  BP runs on the coarsest level from uniform
 // messages, then each finer level starts from the coarser level's final
 // messages copied by direction (the message into (r, c) from side s starts as
 // the one into (r/2, c/2) from side s; uniform where the coarse node has no
@@ -18,32 +19,40 @@
 
 namespace {
 
-// One warp per coarse node: the product of the block's unaries, divided by
-// its maximum over labels.  BP is unchanged by a per-node scale of g, and the
-// scaling keeps the product of 4^l pixel unaries inside FP32's range.
-__global__ void coarsen_f32_kernel(const float *fine, float *coarse, int Wf, int Hf, int Wc, int Hc, int M, int Mp) {
+// One warp per coarse node.  The coarse unary is the product of the block's
+// unaries up to a per-node scale (BP does not see that scale).  It is built in
+// logs: lu_coarse(x) = sum over the block of lu_fine(x), minus its maximum over
+// x, so lu <= 0 stays finite at every level and g = exp(lu) has maximum 1 --
+// the product of 4^l pixel unaries would leave FP32's range.  `fine_log` is
+// the finer level's log unary, or NULL on the first level (then log g of the
+// grid's own unary is taken).
+__global__ void coarsen_f32_kernel(const float *fine_g, const float *fine_log, float *coarse_g, float *coarse_log,
+                                   int Wf, int Hf, int Wc, int Hc, int M, int Mp) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long node = warp; node < (long long)Wc * Hc; node += nwarps) {
         const int r = (int)(node / Wc), c = (int)(node - (long long)r * Wc);
-        float mx = 0.f;
-        for (int x = lane; x < Mp; x += 32) {
-            float p = 0.f;
-            if (x < M) {
-                p = 1.f;
-                for (int dr = 0; dr < 2; ++dr)
-                    for (int dc = 0; dc < 2; ++dc) {
-                        const int fr = 2 * r + dr, fc = 2 * c + dc;
-                        if (fr < Hf && fc < Wf) p *= fine[((long long)fr * Wf + fc) * Mp + x];
+        float mx = -3.0e38f;
+        for (int x = lane; x < M; x += 32) {
+            float sl = 0.f;
+            for (int dr = 0; dr < 2; ++dr)
+                for (int dc = 0; dc < 2; ++dc) {
+                    const int fr = 2 * r + dr, fc = 2 * c + dc;
+                    if (fr < Hf && fc < Wf) {
+                        const long long o = ((long long)fr * Wf + fc) * Mp + x;
+                        sl += fine_log ? fine_log[o] : logf(fine_g[o]);
                     }
-            }
-            coarse[node * Mp + x] = p;
-            mx = fmaxf(mx, p);
+                }
+            coarse_log[node * Mp + x] = sl;
+            mx = fmaxf(mx, sl);
         }
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const float inv = mx > 0.f ? 1.f / mx : 1.f;
-        for (int x = lane; x < Mp; x += 32) coarse[node * Mp + x] *= inv;
+        for (int x = lane; x < Mp; x += 32) {
+            const float lv = x < M ? coarse_log[node * Mp + x] - mx : -3.0e38f;
+            coarse_log[node * Mp + x] = x < M ? lv : 0.f;
+            coarse_g[node * Mp + x] = x < M ? expf(lv) : 0.f;
+        }
     }
 }
 
@@ -139,9 +148,13 @@ extern "C" bp_status bp_iterate_multiscale(bp_handle h, int n_levels, const int 
         bp_set_persistent(c, h->persistent);
         const bp_ctx *f = l == 1 ? h : h->levels[l - 2];
         const long long n = (long long)c->W * c->H * c->Mp;
-        if (h->dtype == BP_F32)
+        if (h->dtype == BP_F32) {
+            if (!c->ms_logu)
+                if (bp_status st2 = bpg_ensure_buffer(c, &c->ms_logu, (size_t)n * 4, "level log unary")) return st2;
             coarsen_f32_kernel<<<bpg::grid_for((long long)c->W * c->H * 32, 256), 256, 0, h->stream>>>(
-                (const float *)f->unary, (float *)c->unary, f->W, f->H, c->W, c->H, h->M, h->Mp);
+                (const float *)f->unary, l == 1 ? nullptr : (const float *)f->ms_logu, (float *)c->unary,
+                (float *)c->ms_logu, f->W, f->H, c->W, c->H, h->M, h->Mp);
+        }
         else
             coarsen_i32_kernel<<<bpg::grid_for(n, 256), 256, 0, h->stream>>>(
                 (const int32_t *)f->unary, (int32_t *)c->unary, f->W, f->H, c->W, c->H, h->M, h->Mp);

@@ -58,3 +58,20 @@ def test_one_level_is_bp_iterate():
     a = _gpu(E, bp.BP_I32, tabi, cfg.T, ebar, [6], bp.BP_MAX, "sync")
     b = H.run_gpu_min(E, tabi, cfg.T, ebar, 6, "sync")
     np.testing.assert_array_equal(a[0], b[0])
+
+
+def test_deep_pyramid_keeps_the_coarse_unaries_in_range():
+    """Six levels on 1280 x 720 (the coarsest node covers 32 x 32 pixels, a
+    product of 1024 unaries): every level must stay finite and the fine result
+    must match the oracle's."""
+    from paper_1010_0012_gb300 import bp
+    import dataclasses
+    cfg = dataclasses.replace(wl.CONFIGS["grid1280x720_m128"], W=160, H=96)
+    st, g, E = H.stereo_inputs(cfg)
+    tab, fbar = wl.pair_table_f32(cfg.alpha, cfg.T)
+    iters = [4, 3, 3, 2, 2, 2]
+    bel, mp, pl = _gpu(g, bp.BP_F32, tab, cfg.T, fbar, iters, bp.BP_SUM, "sync")
+    assert np.all(np.isfinite(bel))
+    F = H.oracle_F_from_table(tab, cfg.T, fbar, cfg.M)
+    p64, b64 = multiscale.multiscale_sum_product(g.astype(np.float64), F, iters, "sync")
+    assert H.node_rel_err(bel, b64) <= H.REL_TOL

@@ -63,3 +63,25 @@ def test_uniform_potential_at_every_level():
     g = rng.uniform(0.05, 1.0, (9, 10, 4))
     planes, bel = multiscale.multiscale_sum_product(g, stereo.pairwise_matrix(0.0, 1, 4), [2, 2, 2])
     np.testing.assert_allclose(bel, g / g.sum(-1, keepdims=True), rtol=1e-12)
+
+
+def test_log_coarsening_is_the_block_product_up_to_scale():
+    rng = np.random.default_rng(8)
+    g = rng.uniform(0.1, 1.0, (5, 6, 4))
+    prod = multiscale.coarsen(g, np.prod)
+    lg = multiscale.coarsen_log(np.log(g))
+    np.testing.assert_allclose(np.exp(lg), prod / prod.max(-1, keepdims=True), rtol=1e-13)
+    assert np.all(lg.max(-1) == 0.0)
+
+
+def test_per_node_unary_scale_does_not_change_bp():
+    """The reason coarse unaries may be rescaled: scaling g_i by any positive
+    constant leaves every normalised message and belief unchanged."""
+    rng = np.random.default_rng(9)
+    g = rng.uniform(0.05, 1.0, (4, 5, 6))
+    F = stereo.pairwise_matrix(0.6, 2, 6)
+    a = grid.grid_sum_product(g, F, 5)
+    b = grid.grid_sum_product(g * rng.uniform(1e-3, 1e3, (4, 5, 1)), F, 5)
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    src, dst, side, rr, cc = grid.grid_edges(5, 4)
+    np.testing.assert_allclose(a[0][side, rr, cc], b[0][side, rr, cc], rtol=1e-12)
