@@ -294,17 +294,23 @@ __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
 }
 
 // ------------------------------------------------------------- min-sum ------
+// When E(0) is the smallest entry of the table (every truncated potential),
+// min_x u(x) = E(0) + min_x h(x) exactly: the pair (x*, x*) with h(x*) minimal
+// is in the band, every band term is >= E(0) + min h, and Ebar >= E(0).  The
+// second reduction is then skipped (`zero_min`).
 template <int L, int C, int T, bool COH>
 struct MinBand {
     static constexpr int V = 4 * C;
     int32_t w[2 * T + 1];
     int32_t ebar;
     bool lab_ok[V];
+    bool zero_min;
     int q;
 
-    __device__ __forceinline__ void setup(const int32_t *wsrc, int32_t eb, int M, int lane_q) {
+    __device__ __forceinline__ void setup(const int32_t *wsrc, int32_t eb, int M, int lane_q, bool zmin = false) {
         q = lane_q;
         ebar = eb;
+        zero_min = zmin;
 #pragma unroll
         for (int i = 0; i < 2 * T + 1; ++i) w[i] = wsrc[i];
 #pragma unroll
@@ -352,7 +358,7 @@ struct MinBand {
                 u[k] = lab_ok[k] ? b : kIntBig;
                 umin = min(umin, u[k]);
             }
-            umin = group_min<L>(umin);
+            umin = zero_min ? w[T] + hmin : group_min<L>(umin);
 #pragma unroll
             for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, u);
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
     constexpr int GPB = kBlock / L;
     const int grp = threadIdx.x / L;
     MinBand<L, C, T, false> band;
-    band.setup(a.w, a.ebar, a.d.M, threadIdx.x & (L - 1));
+    band.setup(a.w, a.ebar, a.d.M, threadIdx.x & (L - 1), a.zero_min != 0);
     const int W = a.d.W;
     const int nslots = num_slots(W, a.d.H, a.parity);
     for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {

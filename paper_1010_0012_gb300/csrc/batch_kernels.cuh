@@ -83,7 +83,7 @@ __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int n
     void *out = parity < 0 ? m->msg[src ^ 1] : m->msg[src];
     if (MIN) {
         MinBand<L, C, T, true> b;
-        b.setup(m->wi, m->ebar, m->M, q);
+        b.setup(m->wi, m->ebar, m->M, q, m->zero_min != 0);
         for (int base = 0; base < count; base += GPB) {
             int r, c;
             const bool valid = base + grp < count && slot_node(node0 + base + grp, nslots, W, parity, r, c);

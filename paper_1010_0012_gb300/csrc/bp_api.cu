@@ -149,6 +149,7 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
                 a.d = h->dims; a.parity = parity; a.T = h->Teff;
                 for (int i = 0; i < 2 * h->Teff + 1; ++i) a.w[i] = h->wi[i];
                 a.ebar = h->ebar;
+                a.zero_min = bpg_zero_min(h->wi) ? 1 : 0;
                 e = launch_band_min(a, h->layout, h->blocks_override, h->stream);
             } else {
                 BandArgsGenericI a{(const int32_t *)h->unary, (const int32_t *)in, (int32_t *)out, h->dims,
@@ -206,6 +207,7 @@ static bp_status persistent_setup(bp_ctx *h) {
     } else {
         for (int i = 0; i < 2 * h->Teff + 1; ++i) m.wi[i] = h->wi[i];
         m.ebar = h->ebar;
+        m.zero_min = bpg_zero_min(h->wi) ? 1 : 0;
     }
     if (bp_status st = ensure_buffer(h, &h->p_mrf, sizeof(BatchMrf), "persistent descriptor")) return st;
     if (bp_status st = ensure_buffer(h, &h->p_bar, 2 * sizeof(unsigned), "barrier words")) return st;
@@ -791,6 +793,15 @@ bp_status bp_set_checkpoint_interval(bp_handle h, int every) {
 }
 
 }  // extern "C"
+
+// True when the centre entry E(0) of a band table (2T+1 entries) is its minimum.
+bool bpg_zero_min(const std::vector<int32_t> &w) {
+    if (w.empty()) return false;
+    const int c = (int)w.size() / 2;
+    for (int32_t v : w)
+        if (v < w[c]) return false;
+    return true;
+}
 
 // Value of the pairwise potential at (x_i, x_j) as the handle holds it: the
 // band table or the sparse list, fbar (Ebar) elsewhere.

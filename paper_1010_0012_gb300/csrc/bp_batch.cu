@@ -267,7 +267,12 @@ bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void 
             const int32_t *t = (const int32_t *)d.host_table;
             mm.tablei.assign(t, t + 2 * d.T + 1);
             x.ebar = (int32_t)d.fbar;
-            for (int dd = -mm.Teff; dd <= mm.Teff; ++dd) x.wi[dd + mm.Teff] = t[dd + d.T];
+            std::vector<int32_t> wv;
+            for (int dd = -mm.Teff; dd <= mm.Teff; ++dd) {
+                x.wi[dd + mm.Teff] = t[dd + d.T];
+                wv.push_back(t[dd + d.T]);
+            }
+            x.zero_min = bpg_zero_min(wv) ? 1 : 0;
         }
     }
     if (st == BP_OK) {

@@ -19,6 +19,7 @@ struct BatchMrf {
     float fbar;
     int32_t wi[2 * kTMaxFast + 1];  // E(d) (min-sum)
     int32_t ebar;
+    int zero_min;                   // 1 if E(0) is the table's minimum
 };
 
 // A run of `count` consecutive slots of one MRF: nodes for a synchronous

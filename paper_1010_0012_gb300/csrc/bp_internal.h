@@ -42,6 +42,7 @@ struct BandArgsI {
     int T;
     int32_t w[2 * kTMaxFast + 1];  // E(d), d = -T..T
     int32_t ebar;
+    int zero_min;                  // 1 if E(0) is the table's minimum
 };
 
 // Shared-memory O(mM) kernels for any T (table on the device).
