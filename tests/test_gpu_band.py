@@ -217,6 +217,7 @@ def test_persistent_issue_is_one_launch_per_call():
     G.set_unary(torch.from_numpy(E).cuda())
     tabi, ebar = wl.pair_table_i32(cfg.alpha, cfg.T)
     G.set_potential(tabi, cfg.T, ebar)
+    bp.bp_set_persistent(G.h, 1)
     G.reset()
     G.iterate(0, bp.BP_MAX)
     n0 = G.launches
