@@ -69,9 +69,10 @@ __device__ __forceinline__ bool batch_grid_barrier(unsigned *count, unsigned *ge
 
 // parity < 0: synchronous (read msg[src], write msg[src ^ 1]); parity 0/1:
 // red-black half-step in place on msg[src], slots as in slot_node.
-template <int L, int C, int T, bool MIN>
+template <int L, int C, int T, bool MIN, bool RB>
 __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int node0, int count, int src,
-                                           int parity) {
+                                           int parity_rt) {
+    const int parity = RB ? parity_rt : -1;
     constexpr int GPB = kBlock / L;
     const int grp = threadIdx.x / L;
     const int q = threadIdx.x & (L - 1);
@@ -85,71 +86,87 @@ __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int n
         MinBand<L, C, T, true> b;
         b.setup(m->wi, m->ebar, m->M, q, m->zero_min != 0);
         for (int base = 0; base < count; base += GPB) {
-            int r, c;
-            const bool valid = base + grp < count && slot_node(node0 + base + grp, nslots, W, parity, r, c);
+            int r = 0, c = 0;
+            bool valid = base + grp < count;
+            if (RB) {
+                valid = valid && slot_node(node0 + base + grp, nslots, W, parity, r, c);
+            } else if (valid) {
+                const int n = node0 + base + grp;
+                r = n / W;
+                c = n - r * W;
+            }
             b.node((const int32_t *)un, (const int32_t *)in, (int32_t *)out, W, H, Mp, plane, r, c, valid);
         }
     } else {
         SumBand<L, C, T, false, true> b;
         b.setup(m->wf, m->fbar, m->M, q);
         for (int base = 0; base < count; base += GPB) {
-            int r, c;
-            const bool valid = base + grp < count && slot_node(node0 + base + grp, nslots, W, parity, r, c);
+            int r = 0, c = 0;
+            bool valid = base + grp < count;
+            if (RB) {
+                valid = valid && slot_node(node0 + base + grp, nslots, W, parity, r, c);
+            } else if (valid) {
+                const int n = node0 + base + grp;
+                r = n / W;
+                c = n - r * W;
+            }
             b.node((const float *)un, (const float *)in, (float *)out, W, H, Mp, plane, r, c, valid);
         }
     }
 }
 
-template <int L, int C, bool MIN>
+template <int L, int C, bool MIN, bool RB>
 __device__ __forceinline__ void batch_item_t(const BatchMrf *__restrict__ m, int node0, int count, int src,
                                              int parity) {
     switch (m->T) {
-        case 0: batch_item<L, C, 0, MIN>(m, node0, count, src, parity); break;
-        case 1: batch_item<L, C, 1, MIN>(m, node0, count, src, parity); break;
-        case 2: batch_item<L, C, 2, MIN>(m, node0, count, src, parity); break;
-        case 3: batch_item<L, C, 3, MIN>(m, node0, count, src, parity); break;
-        case 4: batch_item<L, C, 4, MIN>(m, node0, count, src, parity); break;
-        case 5: batch_item<L, C, 5, MIN>(m, node0, count, src, parity); break;
-        case 6: batch_item<L, C, 6, MIN>(m, node0, count, src, parity); break;
-        case 7: batch_item<L, C, 7, MIN>(m, node0, count, src, parity); break;
-        default: batch_item<L, C, 8, MIN>(m, node0, count, src, parity); break;
+        case 0: batch_item<L, C, 0, MIN, RB>(m, node0, count, src, parity); break;
+        case 1: batch_item<L, C, 1, MIN, RB>(m, node0, count, src, parity); break;
+        case 2: batch_item<L, C, 2, MIN, RB>(m, node0, count, src, parity); break;
+        case 3: batch_item<L, C, 3, MIN, RB>(m, node0, count, src, parity); break;
+        case 4: batch_item<L, C, 4, MIN, RB>(m, node0, count, src, parity); break;
+        case 5: batch_item<L, C, 5, MIN, RB>(m, node0, count, src, parity); break;
+        case 6: batch_item<L, C, 6, MIN, RB>(m, node0, count, src, parity); break;
+        case 7: batch_item<L, C, 7, MIN, RB>(m, node0, count, src, parity); break;
+        default: batch_item<L, C, 8, MIN, RB>(m, node0, count, src, parity); break;
     }
 }
 
 // Family 1: the fewest labels per lane (C = 1 up to 128 labels);
 // family 2: two 4-label chunks per lane.  Padded label counts 16..256.
-template <int FAM, bool MIN>
+template <int FAM, bool MIN, bool RB>
 __device__ __forceinline__ void batch_dispatch(const BatchMrf *__restrict__ m, int node0, int count, int src,
                                                int parity) {
     if (FAM == 1) {
         switch (m->Mp) {
-            case 16: batch_item_t<4, 1, MIN>(m, node0, count, src, parity); break;
-            case 32: batch_item_t<8, 1, MIN>(m, node0, count, src, parity); break;
-            case 64: batch_item_t<16, 1, MIN>(m, node0, count, src, parity); break;
-            case 128: batch_item_t<32, 1, MIN>(m, node0, count, src, parity); break;
-            default: batch_item_t<32, 2, MIN>(m, node0, count, src, parity); break;
+            case 16: batch_item_t<4, 1, MIN, RB>(m, node0, count, src, parity); break;
+            case 32: batch_item_t<8, 1, MIN, RB>(m, node0, count, src, parity); break;
+            case 64: batch_item_t<16, 1, MIN, RB>(m, node0, count, src, parity); break;
+            case 128: batch_item_t<32, 1, MIN, RB>(m, node0, count, src, parity); break;
+            default: batch_item_t<32, 2, MIN, RB>(m, node0, count, src, parity); break;
         }
     } else {
         switch (m->Mp) {
-            case 16: batch_item_t<2, 2, MIN>(m, node0, count, src, parity); break;
-            case 32: batch_item_t<4, 2, MIN>(m, node0, count, src, parity); break;
-            case 64: batch_item_t<8, 2, MIN>(m, node0, count, src, parity); break;
-            case 128: batch_item_t<16, 2, MIN>(m, node0, count, src, parity); break;
-            default: batch_item_t<32, 2, MIN>(m, node0, count, src, parity); break;
+            case 16: batch_item_t<2, 2, MIN, RB>(m, node0, count, src, parity); break;
+            case 32: batch_item_t<4, 2, MIN, RB>(m, node0, count, src, parity); break;
+            case 64: batch_item_t<8, 2, MIN, RB>(m, node0, count, src, parity); break;
+            case 128: batch_item_t<16, 2, MIN, RB>(m, node0, count, src, parity); break;
+            default: batch_item_t<32, 2, MIN, RB>(m, node0, count, src, parity); break;
         }
     }
 }
 
-template <int FAM, bool MIN>
+// RB: the red-black form (two in-place half-steps per iteration), compiled
+// separately so that the synchronous batch kernel keeps its registers.
+template <int FAM, bool MIN, bool RB>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
-    const int phases = a.redblack ? 2 : 1;
+    const int phases = RB ? 2 : 1;
     const int total = a.n_iters * phases;
     for (int step = 0; step < total; ++step) {
-        const int parity = a.redblack ? (step & 1) : -1;
-        const int src = a.redblack ? a.start_buf : ((a.start_buf + step) & 1);
+        const int parity = RB ? (step & 1) : -1;
+        const int src = RB ? a.start_buf : ((a.start_buf + step) & 1);
         for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
             const BatchItem item = a.items[it];
-            batch_dispatch<FAM, MIN>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
+            batch_dispatch<FAM, MIN, RB>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
         }
         if (step + 1 < total) {
             if (!batch_grid_barrier(a.bar_count, a.bar_gen, gridDim.x + a.extra_arrivals, a.limit_ns, a.status))

@@ -4,8 +4,9 @@
 
 namespace bpg {
 
-static const void *batch_min_fn(int family) {
-    return family == 2 ? (const void *)batch_kernel<2, true> : (const void *)batch_kernel<1, true>;
+static const void *batch_min_fn(int family, bool redblack = false) {
+    if (redblack) return (const void *)batch_kernel<1, true, true>;
+    return family == 2 ? (const void *)batch_kernel<2, true, false> : (const void *)batch_kernel<1, true, false>;
 }
 
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s) {
@@ -19,9 +20,11 @@ cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStr
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {const_cast<BatchArgs *>(&a)};
-    return cudaLaunchKernelExC(&cfg, batch_min_fn(family), args);
+    return cudaLaunchKernelExC(&cfg, batch_min_fn(family, a.redblack != 0), args);
 }
 
-int batch_max_blocks_min(int family) { return device_sm_count() * blocks_per_sm(batch_min_fn(family)); }
+int batch_max_blocks_min(int family, bool redblack) {
+    return device_sm_count() * blocks_per_sm(batch_min_fn(family, redblack));
+}
 
 }  // namespace bpg

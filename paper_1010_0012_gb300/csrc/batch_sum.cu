@@ -4,8 +4,9 @@
 
 namespace bpg {
 
-static const void *batch_sum_fn(int family) {
-    return family == 2 ? (const void *)batch_kernel<2, false> : (const void *)batch_kernel<1, false>;
+static const void *batch_sum_fn(int family, bool redblack = false) {
+    if (redblack) return (const void *)batch_kernel<1, false, true>;
+    return family == 2 ? (const void *)batch_kernel<2, false, false> : (const void *)batch_kernel<1, false, false>;
 }
 
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s) {
@@ -19,9 +20,11 @@ cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStr
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {const_cast<BatchArgs *>(&a)};
-    return cudaLaunchKernelExC(&cfg, batch_sum_fn(family), args);
+    return cudaLaunchKernelExC(&cfg, batch_sum_fn(family, a.redblack != 0), args);
 }
 
-int batch_max_blocks_sum(int family) { return device_sm_count() * blocks_per_sm(batch_sum_fn(family)); }
+int batch_max_blocks_sum(int family, bool redblack) {
+    return device_sm_count() * blocks_per_sm(batch_sum_fn(family, redblack));
+}
 
 }  // namespace bpg

@@ -21,8 +21,8 @@
 namespace bpg {
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
-int batch_max_blocks_sum(int family);
-int batch_max_blocks_min(int family);
+int batch_max_blocks_sum(int family, bool redblack = false);
+int batch_max_blocks_min(int family, bool redblack = false);
 }  // namespace bpg
 
 using namespace bpg;
@@ -211,7 +211,8 @@ static bp_status persistent_setup(bp_ctx *h) {
     }
     if (bp_status st = ensure_buffer(h, &h->p_mrf, sizeof(BatchMrf), "persistent descriptor")) return st;
     if (bp_status st = ensure_buffer(h, &h->p_bar, 2 * sizeof(unsigned), "barrier words")) return st;
-    const int maxb = h->dtype == BP_I32 ? batch_max_blocks_min(1) : batch_max_blocks_sum(1);
+    const int maxb = h->dtype == BP_I32 ? std::max(batch_max_blocks_min(1, false), batch_max_blocks_min(1, true))
+                                        : std::max(batch_max_blocks_sum(1, false), batch_max_blocks_sum(1, true));
     const int gpb = kBlock / batch_lanes_per_node(1, h->Mp);
     for (int sched = 0; sched < 2; ++sched) {
         const int nslots = sched == BP_REDBLACK ? ((h->W + 1) / 2) * h->H : h->W * h->H;
@@ -250,7 +251,8 @@ static cudaError_t issue_persistent(bp_ctx *h, int n, int sched, int cur) {
     a.status = h->d_status;
     cudaError_t e = cudaMemsetAsync(h->p_bar, 0, sizeof(unsigned), h->stream);
     if (e != cudaSuccess) return e;
-    const int maxb = h->dtype == BP_I32 ? batch_max_blocks_min(1) : batch_max_blocks_sum(1);
+    const bool rb = sched == BP_REDBLACK;
+    const int maxb = h->dtype == BP_I32 ? batch_max_blocks_min(1, rb) : batch_max_blocks_sum(1, rb);
     const int blocks = std::max(1, std::min(maxb, a.n_items));
     return h->dtype == BP_I32 ? launch_batch_min(a, 1, blocks, h->stream) : launch_batch_sum(a, 1, blocks, h->stream);
 }

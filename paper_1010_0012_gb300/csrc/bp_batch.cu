@@ -24,8 +24,8 @@ using namespace bpg;
 namespace bpg {
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
-int batch_max_blocks_sum(int family);
-int batch_max_blocks_min(int family);
+int batch_max_blocks_sum(int family, bool redblack = false);
+int batch_max_blocks_min(int family, bool redblack = false);
 
 int batch_lanes_per_node(int family, int Mp) {
     if (family == 1) return Mp >= 256 ? 32 : Mp / 4;
