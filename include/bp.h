@@ -265,6 +265,44 @@ void bp_batch_destroy(bp_batch b);
  *    kernel's grid barrier even on 32 x 32 grids).  Results are identical. */
 bp_status bp_set_persistent(bp_handle h, int mode);
 
+/* ---- factor graphs with three-variable factors (Sec. 7) --------------------
+ * Variables v = 0..n_vars-1 with M labels and unaries g_v (or energies E_v);
+ * factors a = 0..n_factors-1, each joining the three distinct variables
+ * host_factor_vars[3a .. 3a+2] (slots 0, 1, 2), all sharing one potential
+ * f(x_0, x_1, x_2) that equals fbar except on C listed compatible triplets.
+ * A flooding iteration updates every variable-to-factor message, then every
+ * factor-to-variable message:
+ *   m_{a->v}(x_s) = sum over listed triplets with that x_s of [f - fbar] n_u n_w
+ *                   + fbar (sum n_u)(sum n_w)                      O(C + M), not O(M^3)
+ * (min-sum: min over listed triplets of E + n_u + n_w, against Ebar + min n_u
+ * + min n_w; needs E <= Ebar).  Messages are normalised (sum 1 / minimum 0).
+ * 2 <= M <= 256; a variable may belong to at most 16 factors. */
+typedef struct bp_fg_ctx *bp_factor_graph;
+
+bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_factor_vars, bp_dtype dtype,
+                       void *cuda_stream, bp_factor_graph *out);
+/* dev_unary [n_vars][M]: float32 g > 0 or int32 energies; copied. */
+bp_status bp_fg_set_unary(bp_factor_graph g, const void *dev_unary);
+/* host_triplets [C][3] distinct (x_0, x_1, x_2) in [0, M); host_vals [C] f
+ * (float32) or E (int32); fbar (or the integer Ebar) elsewhere.
+ * BP_ERR_POTENTIAL in max mode if some E > Ebar. */
+bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplets, const void *host_vals,
+                           double fbar);
+bp_status bp_fg_reset_messages(bp_factor_graph g);
+/* n_iters flooding iterations, mode BP_SUM (float32) or BP_MAX (int32). */
+bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode);
+/* The same iterations with the standard O(M^3) factor update, for comparison. */
+bp_status bp_fg_iterate_dense(bp_factor_graph g, int n_iters, int mode);
+/* Beliefs [n_vars][M] (normalised float32, or int32 E_v + sum of messages) and
+ * MAP labels (nullable), lowest label on ties. */
+bp_status bp_fg_beliefs(bp_factor_graph g, void *dev_out, int32_t *dev_map);
+/* Factor-to-variable messages [n_factors][3][M] (slot order). */
+bp_status bp_fg_get_messages(bp_factor_graph g, void *dev_out);
+bp_status bp_fg_sync(bp_factor_graph g);
+const char *bp_fg_last_error(bp_factor_graph g);
+long long bp_fg_launch_count(bp_factor_graph g);
+void bp_fg_destroy(bp_factor_graph g);
+
 /* Number of kernel launches the library issued on this handle so far. */
 long long bp_launch_count(bp_handle h);
 

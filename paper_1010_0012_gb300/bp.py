@@ -76,6 +76,18 @@ def _load():
         "bp_batch_last_error": ([P], ctypes.c_char_p),
         "bp_batch_launch_count": ([P], ctypes.c_longlong),
         "bp_batch_destroy": ([P], None),
+        "bp_fg_create": ([I, I, I, P, I, P, ctypes.POINTER(P)], I),
+        "bp_fg_set_unary": ([P, P], I),
+        "bp_fg_set_factor": ([P, I, P, P, D], I),
+        "bp_fg_reset_messages": ([P], I),
+        "bp_fg_iterate": ([P, I, I], I),
+        "bp_fg_iterate_dense": ([P, I, I], I),
+        "bp_fg_beliefs": ([P, P, P], I),
+        "bp_fg_get_messages": ([P, P], I),
+        "bp_fg_sync": ([P], I),
+        "bp_fg_last_error": ([P], ctypes.c_char_p),
+        "bp_fg_launch_count": ([P], ctypes.c_longlong),
+        "bp_fg_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -334,6 +346,74 @@ def bp_batch_launch_count(b):
 
 def bp_batch_destroy(b):
     _lib.bp_batch_destroy(b)
+
+
+# ---- factor graphs ------------------------------------------------------------------
+
+def _fcheck(g, st):
+    if st != BP_OK:
+        raise BPError(st, _lib.bp_fg_last_error(g).decode())
+
+
+def bp_fg_create(n_vars, M, factor_vars, dtype, stream=None):
+    import numpy as np
+    fv = np.ascontiguousarray(factor_vars, dtype=np.int32).reshape(-1, 3)
+    g = ctypes.c_void_p()
+    st = _lib.bp_fg_create(int(n_vars), int(M), int(fv.shape[0]), fv.ctypes.data_as(ctypes.c_void_p), int(dtype),
+                           _stream_ptr(stream), ctypes.byref(g))
+    _fcheck(None, st)
+    return g
+
+
+def bp_fg_set_unary(g, unary: torch.Tensor):
+    _fcheck(g, _lib.bp_fg_set_unary(g, ctypes.c_void_p(unary.data_ptr())))
+
+
+def bp_fg_set_factor(g, triplets, vals, fbar, dtype):
+    import numpy as np
+    t = np.ascontiguousarray(triplets, dtype=np.int32).reshape(-1, 3)
+    v = np.ascontiguousarray(vals, dtype=np.float32 if dtype == BP_F32 else np.int32)
+    if v.size != t.shape[0]:
+        raise ValueError("one value per triplet")
+    _fcheck(g, _lib.bp_fg_set_factor(g, int(t.shape[0]), t.ctypes.data_as(ctypes.c_void_p),
+                                     v.ctypes.data_as(ctypes.c_void_p), float(fbar)))
+
+
+def bp_fg_reset_messages(g):
+    _fcheck(g, _lib.bp_fg_reset_messages(g))
+
+
+def bp_fg_iterate(g, n_iters, mode):
+    _fcheck(g, _lib.bp_fg_iterate(g, int(n_iters), int(mode)))
+
+
+def bp_fg_iterate_dense(g, n_iters, mode):
+    _fcheck(g, _lib.bp_fg_iterate_dense(g, int(n_iters), int(mode)))
+
+
+def bp_fg_beliefs(g, out: torch.Tensor, map_out: Optional[torch.Tensor] = None):
+    mp = None if map_out is None else _dptr(map_out, torch.int32)
+    _fcheck(g, _lib.bp_fg_beliefs(g, ctypes.c_void_p(out.data_ptr()), mp))
+
+
+def bp_fg_get_messages(g, out: torch.Tensor):
+    _fcheck(g, _lib.bp_fg_get_messages(g, ctypes.c_void_p(out.data_ptr())))
+
+
+def bp_fg_sync(g):
+    _fcheck(g, _lib.bp_fg_sync(g))
+
+
+def bp_fg_last_error(g=None):
+    return _lib.bp_fg_last_error(g).decode()
+
+
+def bp_fg_launch_count(g):
+    return _lib.bp_fg_launch_count(g)
+
+
+def bp_fg_destroy(g):
+    _lib.bp_fg_destroy(g)
 
 
 # ---- a thin owner of one handle -------------------------------------------------

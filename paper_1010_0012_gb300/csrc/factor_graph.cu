@@ -1,0 +1,605 @@
+// Factor-graph BP with three-variable factors whose compatible triplets are
+// sparse (Sec. 7): with f = fbar outside a set of C triplets, the message from
+// a factor to its slot-s variable is
+//   m(x_s) = sum_{compatible (x_0, x_1, x_2) with that x_s} [f - fbar] n_u(x_u) n_w(x_w)
+//            + fbar (sum_x n_u(x)) (sum_x n_w(x))
+// (u, w the other two slots): O(C + M) instead of the O(M^3) of the standard
+// update, and for min-sum (energies, E <= Ebar)
+//   m(x_s) = min( min_{compatible} [E + n_u(x_u) + n_w(x_w)], Ebar + min n_u + min n_w ).
+// Declarations and the contract of every call are in include/bp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/bp.h"
+#include "bp_internal.h"
+
+namespace {
+
+constexpr int kFgBlock = 256;
+constexpr int kFgWarps = kFgBlock / 32;
+constexpr int kMaxDegree = 16;
+constexpr int32_t kBig = 1 << 30;
+
+struct FgDims {
+    int n_vars, n_factors, M, Mp;
+};
+
+// ---- variable -> factor: n = unary x the other incoming factor messages ------
+template <bool MIN, typename E>
+__global__ void v2f_kernel(const E *unary, const int32_t *var_ptr, const int32_t *var_inc, const E *m_fv, E *n_vf,
+                           FgDims d) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long v = warp; v < d.n_vars; v += nw) {
+        const int p0 = var_ptr[v], deg = var_ptr[v + 1] - p0;
+        // normaliser (sum) or minimum (min-sum) of every outgoing message
+        E acc[kMaxDegree];
+#pragma unroll
+        for (int k = 0; k < kMaxDegree; ++k) acc[k] = MIN ? E(kBig) : E(0);
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int x = lane; x < d.Mp; x += 32) {
+                const E u = unary[v * d.Mp + x];
+#pragma unroll
+                for (int k = 0; k < kMaxDegree; ++k) {
+                    if (k >= deg) break;
+                    E p = u;
+                    for (int j = 0; j < deg; ++j)
+                        if (j != k) {
+                            const E mj = m_fv[(long long)var_inc[p0 + j] * d.Mp + x];
+                            if (MIN) p += mj; else p *= mj;
+                        }
+                    if (x >= d.M) p = MIN ? E(kBig) : E(0);
+                    if (pass == 0) {
+                        if (MIN) acc[k] = p < acc[k] ? p : acc[k]; else acc[k] += p;
+                    } else {
+                        E out;
+                        if (MIN) out = x < d.M ? p - acc[k] : E(0);
+                        else out = p / acc[k];
+                        n_vf[(long long)var_inc[p0 + k] * d.Mp + x] = out;
+                    }
+                }
+            }
+            if (pass == 0)
+#pragma unroll
+                for (int k = 0; k < kMaxDegree; ++k) {
+                    if (k >= deg) break;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const E y = __shfl_xor_sync(0xffffffffu, acc[k], o);
+                        if (MIN) acc[k] = y < acc[k] ? y : acc[k]; else acc[k] += y;
+                    }
+                }
+        }
+    }
+}
+
+// ---- factor -> variable: the O(C + M) update -----------------------------------
+// Block shared memory holds, per slot s, the triplets ordered by x_s (CSR
+// ptr_s[M+1]) as (other labels packed x_u | x_w << 16, weight bits); each warp
+// stages its factor's three incoming vectors.
+template <bool MIN, typename E>
+__global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, const int32_t *ptr, const int2 *ent,
+                                                       int C, FgDims d, E fbar_or_ebar) {
+    extern __shared__ uint8_t sm[];
+    const int M = d.M, Mp = d.Mp;
+    int *sptr = (int *)sm;                                        // [3][M + 1]
+    int2 *sent = (int2 *)(sm + ((3 * (M + 1) * 4 + 15) & ~15));   // [3][C]
+    E *sn = (E *)((uint8_t *)sent + (size_t)3 * C * 8);           // [warps][3][Mp]
+    for (int i = threadIdx.x; i < 3 * (M + 1); i += kFgBlock) sptr[i] = ptr[i];
+    for (int i = threadIdx.x; i < 3 * C; i += kFgBlock) sent[i] = ent[i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    E *n = sn + warp * 3 * Mp;
+    const long long gw = (long long)blockIdx.x * kFgWarps + warp, nw = (long long)gridDim.x * kFgWarps;
+    for (long long a = gw; a < d.n_factors; a += nw) {
+        E red[3];
+        for (int s = 0; s < 3; ++s) red[s] = MIN ? E(kBig) : E(0);
+        for (int x = lane; x < Mp; x += 32)
+            for (int s = 0; s < 3; ++s) {
+                E v = n_vf[(a * 3 + s) * Mp + x];
+                if (MIN && x >= M) v = E(kBig);
+                n[s * Mp + x] = v;
+                if (x < M) {
+                    if (MIN) red[s] = v < red[s] ? v : red[s]; else red[s] += v;
+                }
+            }
+        for (int s = 0; s < 3; ++s)
+            for (int o = 16; o > 0; o >>= 1) {
+                const E y = __shfl_xor_sync(0xffffffffu, red[s], o);
+                if (MIN) red[s] = y < red[s] ? y : red[s]; else red[s] += y;
+            }
+        __syncwarp();
+        for (int s = 0; s < 3; ++s) {
+            const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;   // the other two slots, in order
+            const E flat = MIN ? fbar_or_ebar + red[u] + red[w] : fbar_or_ebar * red[u] * red[w];
+            E norm = MIN ? E(kBig) : E(0);
+            E outv[8];   // M <= 256: at most 8 labels per lane
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = lane + 32 * k;
+                if (k * 32 >= Mp) break;
+                E acc = MIN ? flat : E(0);
+                if (x < M) {
+                    for (int p = sptr[s * (M + 1) + x]; p < sptr[s * (M + 1) + x + 1]; ++p) {
+                        const int2 e = sent[(size_t)s * C + p];
+                        const int xu = e.x & 0xffff, xw = e.x >> 16;
+                        if (MIN) {
+                            const E t = e.y + n[u * Mp + xu] + n[w * Mp + xw];
+                            acc = t < acc ? t : acc;
+                        } else {
+                            acc = fmaf(__int_as_float(e.y), n[u * Mp + xu] * n[w * Mp + xw], acc);
+                        }
+                    }
+                    if (!MIN) acc += flat;
+                    if (MIN) norm = acc < norm ? acc : norm; else norm += acc;
+                }
+                outv[k] = acc;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const E y = __shfl_xor_sync(0xffffffffu, norm, o);
+                if (MIN) norm = y < norm ? y : norm; else norm += y;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = lane + 32 * k;
+                if (k * 32 >= Mp) break;
+                if (x < Mp) {
+                    E v;
+                    if (MIN) v = x < M ? outv[k] - norm : E(0);
+                    else v = x < M ? outv[k] / norm : E(0);
+                    m_fv[(a * 3 + s) * Mp + x] = v;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---- the standard O(M^3) update on CUDA cores (comparison) ---------------------
+template <bool MIN, typename E>
+__global__ void f2v_dense_kernel(const E *n_vf, E *m_fv, const E *F, FgDims d) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int M = d.M, Mp = d.Mp;
+    for (long long a = warp; a < d.n_factors; a += nw) {
+        const E *n = n_vf + a * 3 * Mp;
+        for (int s = 0; s < 3; ++s) {
+            const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;
+            E norm = MIN ? E(kBig) : E(0);
+            E outv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = lane + 32 * k;
+                if (k * 32 >= Mp) break;
+                E acc = MIN ? E(kBig) : E(0);
+                if (x < M) {
+                    for (int xu = 0; xu < M; ++xu)
+                        for (int xw = 0; xw < M; ++xw) {
+                            int idx[3];
+                            idx[s] = x; idx[u] = xu; idx[w] = xw;
+                            const E f = F[((long long)idx[0] * M + idx[1]) * M + idx[2]];
+                            if (MIN) {
+                                const E t = f + n[u * Mp + xu] + n[w * Mp + xw];
+                                acc = t < acc ? t : acc;
+                            } else {
+                                acc = fmaf(f, n[u * Mp + xu] * n[w * Mp + xw], acc);
+                            }
+                        }
+                    if (MIN) norm = acc < norm ? acc : norm; else norm += acc;
+                }
+                outv[k] = acc;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const E y = __shfl_xor_sync(0xffffffffu, norm, o);
+                if (MIN) norm = y < norm ? y : norm; else norm += y;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int x = lane + 32 * k;
+                if (k * 32 >= Mp) break;
+                if (x < Mp) {
+                    E v;
+                    if (MIN) v = x < M ? outv[k] - norm : E(0);
+                    else v = x < M ? outv[k] / norm : E(0);
+                    m_fv[(a * 3 + s) * Mp + x] = v;
+                }
+            }
+        }
+    }
+}
+
+template <bool MIN, typename E>
+__global__ void fg_beliefs_kernel(const E *unary, const int32_t *var_ptr, const int32_t *var_inc, const E *m_fv,
+                                  FgDims d, E *out, int32_t *map) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long v = warp; v < d.n_vars; v += nw) {
+        const int p0 = var_ptr[v], deg = var_ptr[v + 1] - p0;
+        E z = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            E best = MIN ? E(kBig) : E(-1);
+            int bi = 0x7fffffff;
+            for (int x = lane; x < d.M; x += 32) {
+                E b = unary[v * d.Mp + x];
+                for (int j = 0; j < deg; ++j) {
+                    const E mj = m_fv[(long long)var_inc[p0 + j] * d.Mp + x];
+                    if (MIN) b += mj; else b *= mj;
+                }
+                if (pass == 0) {
+                    if (!MIN) z += b;
+                } else {
+                    if (!MIN) b = b / z;
+                    out[v * d.M + x] = b;
+                    if (MIN ? (b < best) : (b > best)) { best = b; bi = x; }
+                }
+            }
+            if (pass == 0) {
+                for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+            } else {
+                for (int o = 16; o > 0; o >>= 1) {
+                    const E ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if ((MIN ? (ob < best) : (ob > best)) || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                }
+                if (map && lane == 0) map[v] = bi;
+            }
+        }
+    }
+}
+
+template <typename E>
+__global__ void fg_fill_kernel(E *p, long long rows, int M, int Mp, E v) {
+    const long long n = rows * Mp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = (i % Mp) < M ? v : E(0);
+}
+
+template <typename E>
+__global__ void fg_pad_kernel(const E *src, E *dst, long long rows, int M, int Mp) {
+    const long long n = rows * Mp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / Mp;
+        const int x = (int)(i - r * Mp);
+        dst[i] = x < M ? src[r * M + x] : E(0);
+    }
+}
+
+thread_local std::string g_fg_err;
+
+}  // namespace
+
+struct bp_fg_ctx {
+    int n_vars = 0, n_factors = 0, M = 0, Mp = 0;
+    bp_dtype dtype = BP_F32;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void *unary = nullptr;
+    int32_t *var_ptr = nullptr, *var_inc = nullptr;
+    void *m_fv = nullptr, *n_vf = nullptr;
+    int32_t *d_ptr = nullptr;
+    int2 *d_ent = nullptr;
+    void *d_dense = nullptr;
+    int C = 0;
+    double fbar = 0;
+    std::vector<int32_t> trip;   // [C][3]
+    std::vector<float> valf;
+    std::vector<int32_t> vali;
+    bool have_unary = false, have_factor = false, uniform_pending = true;
+    long long launches = 0;
+    std::string err;
+};
+
+static bp_status fgfail(bp_factor_graph g, bp_status st, const std::string &m) {
+    if (g) g->err = m; else g_fg_err = m;
+    return st;
+}
+
+#define FG_CK(g, call)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fgfail((g), e_ == cudaErrorMemoryAllocation ? BP_ERR_OOM : BP_ERR_CUDA,             \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+    } while (0)
+
+static size_t f2v_smem(int M, int Mp, int C, int elem) {
+    return (size_t)((3 * (M + 1) * 4 + 15) & ~15) + (size_t)3 * C * 8 + (size_t)kFgWarps * 3 * Mp * elem;
+}
+
+static int warp_grid(long long items) {
+    long long b = (items * 32 + 255) / 256;
+    const long long cap = (long long)bpg::device_sm_count() * 16;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+extern "C" {
+
+const char *bp_fg_last_error(bp_factor_graph g) { return g ? g->err.c_str() : g_fg_err.c_str(); }
+long long bp_fg_launch_count(bp_factor_graph g) { return g ? g->launches : -1; }
+
+void bp_fg_destroy(bp_factor_graph g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    void *bufs[] = {g->unary, g->var_ptr, g->var_inc, g->m_fv, g->n_vf, g->d_ptr, g->d_ent, g->d_dense};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_factor_vars, bp_dtype dtype,
+                       void *cuda_stream, bp_factor_graph *out) {
+    g_fg_err.clear();
+    if (!out) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: out is NULL");
+    *out = nullptr;
+    if (n_vars < 1 || n_factors < 0 || M < 2 || M > 256 || (n_factors > 0 && !host_factor_vars))
+        return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: need n_vars >= 1, 2 <= M <= 256, factor list");
+    if (dtype != BP_F32 && dtype != BP_I32) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: unknown dtype");
+    if ((long long)n_factors * 3 * 256 >= (1LL << 31) || (long long)n_vars * 256 >= (1LL << 31))
+        return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: graph too large");
+    std::vector<int> deg(n_vars, 0);
+    for (int a = 0; a < n_factors; ++a) {
+        const int32_t *v = host_factor_vars + 3 * a;
+        for (int s = 0; s < 3; ++s)
+            if (v[s] < 0 || v[s] >= n_vars) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: variable out of range");
+        if (v[0] == v[1] || v[0] == v[2] || v[1] == v[2])
+            return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: a factor must join three distinct variables");
+        for (int s = 0; s < 3; ++s)
+            if (++deg[v[s]] > kMaxDegree)
+                return fgfail(nullptr, BP_ERR_UNSUPPORTED, "bp_fg_create: a variable is in more than 16 factors");
+    }
+    bp_factor_graph g = new bp_fg_ctx();
+    g->n_vars = n_vars; g->n_factors = n_factors; g->M = M; g->Mp = (M + 3) & ~3; g->dtype = dtype;
+    if (cuda_stream) g->stream = (cudaStream_t)cuda_stream;
+    else if (cudaStreamCreateWithFlags(&g->stream, cudaStreamDefault) != cudaSuccess) {
+        delete g;
+        return fgfail(nullptr, BP_ERR_CUDA, "bp_fg_create: stream creation failed");
+    } else g->own_stream = true;
+    std::vector<int32_t> ptr(n_vars + 1, 0), inc(3 * (size_t)n_factors);
+    for (int v = 0; v < n_vars; ++v) ptr[v + 1] = ptr[v] + deg[v];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int a = 0; a < n_factors; ++a)
+        for (int s = 0; s < 3; ++s) inc[fill[host_factor_vars[3 * a + s]]++] = 3 * a + s;
+    const size_t msgb = (size_t)(n_factors > 0 ? n_factors : 1) * 3 * g->Mp * 4;
+    bool ok = cudaMalloc(&g->unary, (size_t)n_vars * g->Mp * 4) == cudaSuccess &&
+              cudaMalloc(&g->var_ptr, (n_vars + 1) * 4) == cudaSuccess &&
+              cudaMalloc(&g->var_inc, (inc.size() > 0 ? inc.size() : 1) * 4) == cudaSuccess &&
+              cudaMalloc(&g->m_fv, msgb) == cudaSuccess && cudaMalloc(&g->n_vf, msgb) == cudaSuccess;
+    if (ok) ok = cudaMemcpy(g->var_ptr, ptr.data(), (n_vars + 1) * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                 (inc.empty() || cudaMemcpy(g->var_inc, inc.data(), inc.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess);
+    if (!ok) {
+        cudaGetLastError();
+        bp_fg_destroy(g);
+        return fgfail(nullptr, BP_ERR_OOM, "bp_fg_create: device allocation failed");
+    }
+    *out = g;
+    return BP_OK;
+}
+
+bp_status bp_fg_set_unary(bp_factor_graph g, const void *dev_unary) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_set_unary: NULL graph");
+    g->err.clear();
+    if (!dev_unary) return fgfail(g, BP_ERR_ARG, "bp_fg_set_unary: NULL unary");
+    if (g->dtype == BP_F32)
+        fg_pad_kernel<float><<<bpg::grid_for((long long)g->n_vars * g->Mp, 256), 256, 0, g->stream>>>(
+            (const float *)dev_unary, (float *)g->unary, g->n_vars, g->M, g->Mp);
+    else
+        fg_pad_kernel<int32_t><<<bpg::grid_for((long long)g->n_vars * g->Mp, 256), 256, 0, g->stream>>>(
+            (const int32_t *)dev_unary, (int32_t *)g->unary, g->n_vars, g->M, g->Mp);
+    FG_CK(g, cudaGetLastError());
+    g->launches += 1;
+    g->have_unary = true;
+    return BP_OK;
+}
+
+bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplets, const void *host_vals,
+                           double fbar) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_set_factor: NULL graph");
+    g->err.clear();
+    if (C < 0 || (C > 0 && (!host_triplets || !host_vals)))
+        return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: bad triplet list");
+    if (!std::isfinite(fbar) || fbar < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: fbar must be >= 0");
+    if (f2v_smem(g->M, g->Mp, C, 4) > 220 * 1024)
+        return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: too many compatible triplets for shared memory");
+    std::vector<char> seen((size_t)g->M * g->M * g->M, 0);
+    for (int c = 0; c < C; ++c) {
+        const int32_t *t = host_triplets + 3 * c;
+        for (int s = 0; s < 3; ++s)
+            if (t[s] < 0 || t[s] >= g->M) return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: label out of range");
+        char &z = seen[((size_t)t[0] * g->M + t[1]) * g->M + t[2]];
+        if (z) return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: repeated triplet");
+        z = 1;
+    }
+    std::vector<int32_t> wbits(C);
+    if (g->dtype == BP_F32) {
+        const float *v = (const float *)host_vals;
+        for (int c = 0; c < C; ++c) {
+            if (!std::isfinite(v[c]) || v[c] < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: bad value");
+            const float w = (float)((double)v[c] - (double)(float)fbar);
+            wbits[c] = *reinterpret_cast<const int32_t *>(&w);
+        }
+        g->valf.assign(v, v + C);
+    } else {
+        if (fbar != std::floor(fbar) || fbar >= (double)(1 << 26))
+            return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: Ebar must be an integer in [0, 2^26)");
+        const int32_t *v = (const int32_t *)host_vals;
+        for (int c = 0; c < C; ++c) {
+            if (v[c] < 0 || v[c] >= (1 << 26)) return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: energy out of range");
+            if (v[c] > (int32_t)fbar)
+                return fgfail(g, BP_ERR_POTENTIAL, "bp_fg_set_factor: E > Ebar; the max-product form needs f >= fbar");
+            wbits[c] = v[c];
+        }
+        g->vali.assign(v, v + C);
+    }
+    g->trip.assign(host_triplets, host_triplets + 3 * (size_t)C);
+    // three CSR orders: by x_0, by x_1, by x_2
+    std::vector<int32_t> ptr(3 * (size_t)(g->M + 1), 0);
+    std::vector<int2> ent(3 * (size_t)(C > 0 ? C : 1));
+    for (int s = 0; s < 3; ++s) {
+        int32_t *p = ptr.data() + s * (g->M + 1);
+        for (int c = 0; c < C; ++c) p[host_triplets[3 * c + s] + 1]++;
+        for (int x = 0; x < g->M; ++x) p[x + 1] += p[x];
+        std::vector<int32_t> fillp(p, p + g->M);
+        const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;
+        for (int c = 0; c < C; ++c) {
+            const int32_t *t = host_triplets + 3 * c;
+            ent[(size_t)s * C + fillp[t[s]]++] = make_int2(t[u] | (t[w] << 16), wbits[c]);
+        }
+    }
+    if (g->d_ptr) cudaFree(g->d_ptr);
+    if (g->d_ent) cudaFree(g->d_ent);
+    if (g->d_dense) cudaFree(g->d_dense);
+    g->d_ptr = nullptr; g->d_ent = nullptr; g->d_dense = nullptr;
+    FG_CK(g, cudaMalloc(&g->d_ptr, ptr.size() * 4));
+    FG_CK(g, cudaMalloc(&g->d_ent, ent.size() * sizeof(int2)));
+    FG_CK(g, cudaMemcpy(g->d_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
+    FG_CK(g, cudaMemcpy(g->d_ent, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    g->C = C;
+    g->fbar = fbar;
+    g->have_factor = true;
+    return BP_OK;
+}
+
+bp_status bp_fg_reset_messages(bp_factor_graph g) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_reset_messages: NULL graph");
+    g->uniform_pending = true;
+    return BP_OK;
+}
+
+static bp_status fg_prepare(bp_factor_graph g, int mode) {
+    if (!g->have_unary || !g->have_factor) return fgfail(g, BP_ERR_STATE, "set the unary and the factor first");
+    if ((mode == BP_MAX) != (g->dtype == BP_I32) || (mode != BP_SUM && mode != BP_MAX))
+        return fgfail(g, BP_ERR_ARG, "BP_SUM needs BP_F32, BP_MAX needs BP_I32");
+    if (g->uniform_pending && g->n_factors > 0) {
+        const long long rows = 3LL * g->n_factors;
+        if (g->dtype == BP_F32)
+            fg_fill_kernel<float><<<bpg::grid_for(rows * g->Mp, 256), 256, 0, g->stream>>>((float *)g->m_fv, rows, g->M,
+                                                                                          g->Mp, 1.0f / g->M);
+        else
+            fg_fill_kernel<int32_t><<<bpg::grid_for(rows * g->Mp, 256), 256, 0, g->stream>>>((int32_t *)g->m_fv, rows,
+                                                                                            g->M, g->Mp, 0);
+        FG_CK(g, cudaGetLastError());
+        g->launches += 1;
+    }
+    g->uniform_pending = false;
+    return BP_OK;
+}
+
+static bp_status fg_v2f(bp_factor_graph g) {
+    const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
+    if (g->dtype == BP_F32)
+        v2f_kernel<false, float><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
+            (const float *)g->unary, g->var_ptr, g->var_inc, (const float *)g->m_fv, (float *)g->n_vf, d);
+    else
+        v2f_kernel<true, int32_t><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
+            (const int32_t *)g->unary, g->var_ptr, g->var_inc, (const int32_t *)g->m_fv, (int32_t *)g->n_vf, d);
+    FG_CK(g, cudaGetLastError());
+    g->launches += 1;
+    return BP_OK;
+}
+
+bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_iterate: NULL graph");
+    g->err.clear();
+    if (n_iters < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_iterate: n_iters < 0");
+    if (bp_status st = fg_prepare(g, mode)) return st;
+    if (g->n_factors == 0) return BP_OK;
+    const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
+    const size_t smem = f2v_smem(g->M, g->Mp, g->C, 4);
+    const void *fn = g->dtype == BP_F32 ? (const void *)f2v_kernel<false, float> : (const void *)f2v_kernel<true, int32_t>;
+    FG_CK(g, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFgBlock, smem);
+    long long blocks = (long long)bpg::device_sm_count() * std::max(1, per_sm);
+    blocks = std::min<long long>(blocks, (g->n_factors + kFgWarps - 1) / kFgWarps);
+    for (int it = 0; it < n_iters; ++it) {
+        if (bp_status st = fg_v2f(g)) return st;
+        if (g->dtype == BP_F32)
+            f2v_kernel<false, float><<<(int)blocks, kFgBlock, smem, g->stream>>>(
+                (const float *)g->n_vf, (float *)g->m_fv, g->d_ptr, g->d_ent, g->C, d, (float)g->fbar);
+        else
+            f2v_kernel<true, int32_t><<<(int)blocks, kFgBlock, smem, g->stream>>>(
+                (const int32_t *)g->n_vf, (int32_t *)g->m_fv, g->d_ptr, g->d_ent, g->C, d, (int32_t)g->fbar);
+        FG_CK(g, cudaGetLastError());
+        g->launches += 1;
+    }
+    return BP_OK;
+}
+
+bp_status bp_fg_iterate_dense(bp_factor_graph g, int n_iters, int mode) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_iterate_dense: NULL graph");
+    g->err.clear();
+    if (n_iters < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_iterate_dense: n_iters < 0");
+    if (bp_status st = fg_prepare(g, mode)) return st;
+    if (g->n_factors == 0) return BP_OK;
+    const size_t M = g->M;
+    if (!g->d_dense) {
+        std::vector<float> Ff;
+        std::vector<int32_t> Fi;
+        if (g->dtype == BP_F32) Ff.assign(M * M * M, (float)g->fbar); else Fi.assign(M * M * M, (int32_t)g->fbar);
+        for (int c = 0; c < g->C; ++c) {
+            const size_t idx = ((size_t)g->trip[3 * c] * M + g->trip[3 * c + 1]) * M + g->trip[3 * c + 2];
+            if (g->dtype == BP_F32) Ff[idx] = g->valf[c]; else Fi[idx] = g->vali[c];
+        }
+        FG_CK(g, cudaMalloc(&g->d_dense, M * M * M * 4));
+        FG_CK(g, cudaMemcpy(g->d_dense, g->dtype == BP_F32 ? (const void *)Ff.data() : (const void *)Fi.data(),
+                            M * M * M * 4, cudaMemcpyHostToDevice));
+    }
+    const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
+    for (int it = 0; it < n_iters; ++it) {
+        if (bp_status st = fg_v2f(g)) return st;
+        if (g->dtype == BP_F32)
+            f2v_dense_kernel<false, float><<<warp_grid(g->n_factors), 256, 0, g->stream>>>(
+                (const float *)g->n_vf, (float *)g->m_fv, (const float *)g->d_dense, d);
+        else
+            f2v_dense_kernel<true, int32_t><<<warp_grid(g->n_factors), 256, 0, g->stream>>>(
+                (const int32_t *)g->n_vf, (int32_t *)g->m_fv, (const int32_t *)g->d_dense, d);
+        FG_CK(g, cudaGetLastError());
+        g->launches += 1;
+    }
+    return BP_OK;
+}
+
+bp_status bp_fg_beliefs(bp_factor_graph g, void *dev_out, int32_t *dev_map) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_beliefs: NULL graph");
+    g->err.clear();
+    if (!dev_out) return fgfail(g, BP_ERR_ARG, "bp_fg_beliefs: NULL output");
+    if (bp_status st = fg_prepare(g, g->dtype == BP_F32 ? BP_SUM : BP_MAX)) return st;
+    const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
+    if (g->dtype == BP_F32)
+        fg_beliefs_kernel<false, float><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
+            (const float *)g->unary, g->var_ptr, g->var_inc, (const float *)g->m_fv, d, (float *)dev_out, dev_map);
+    else
+        fg_beliefs_kernel<true, int32_t><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
+            (const int32_t *)g->unary, g->var_ptr, g->var_inc, (const int32_t *)g->m_fv, d, (int32_t *)dev_out, dev_map);
+    FG_CK(g, cudaGetLastError());
+    g->launches += 1;
+    return BP_OK;
+}
+
+bp_status bp_fg_get_messages(bp_factor_graph g, void *dev_out) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_get_messages: NULL graph");
+    g->err.clear();
+    if (!dev_out) return fgfail(g, BP_ERR_ARG, "bp_fg_get_messages: NULL output");
+    if (g->n_factors == 0) return BP_OK;
+    if (g->uniform_pending) return fgfail(g, BP_ERR_STATE, "bp_fg_get_messages: messages not materialised yet");
+    FG_CK(g, bpg::launch_unpad_copy(g->m_fv, dev_out, 3LL * g->n_factors, g->M, g->Mp, g->stream));
+    g->launches += 1;
+    return BP_OK;
+}
+
+bp_status bp_fg_sync(bp_factor_graph g) {
+    if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_sync: NULL graph");
+    FG_CK(g, cudaStreamSynchronize(g->stream));
+    return BP_OK;
+}
+
+}  // extern "C"
