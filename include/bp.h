@@ -47,7 +47,7 @@ typedef enum {
     BP_ERR_OOM = 4,         /* device allocation failed                          */
     BP_ERR_POTENTIAL = 5,   /* max mode with E(d) > Ebar: Eq. 11 needs f >= fbar */
     BP_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                */
-    BP_ERR_UNSUPPORTED = 7  /* valid request this build cannot serve             */
+    BP_ERR_UNSUPPORTED = 7  /* valid request outside what the library serves     */
 } bp_status;
 
 /* Message-passing mode (Sec. 3 and Sec. 5).  BP_LOG and BP_RECORD are flags
