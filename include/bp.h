@@ -179,6 +179,9 @@ void bp_destroy(bp_handle h);
 bp_status bp_set_layout(bp_handle h, int lanes_per_node, int vec_chunks);
 bp_status bp_get_layout(bp_handle h, int *lanes_per_node, int *vec_chunks);
 bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms);
+/* Blocks per launch of the O(mM) register kernels (grid-stride over nodes);
+ * 0 (default) = SM count x resident blocks per SM. */
+bp_status bp_set_grid(bp_handle h, int blocks);
 
 /* Allocation-free dense tensor-core iteration (no counterpart in the paper;
  * an addition for callers that cannot allocate device memory).  Some callers

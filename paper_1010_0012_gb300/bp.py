@@ -54,6 +54,7 @@ def _load():
         "bp_backward": ([P, P, P, P, P], I),
         "bp_set_checkpoint_interval": ([P, I], I),
         "bp_set_persistent": ([P, I], I),
+        "bp_set_grid": ([P, I], I),
         "bp_sync": ([P], I),
         "bp_last_error": ([P], ctypes.c_char_p),
         "bp_destroy": ([P], None),
@@ -215,6 +216,10 @@ def bp_backward(h, dlogb: torch.Tensor, dlogg: torch.Tensor, n_table: int):
 
 def bp_set_checkpoint_interval(h, every):
     _check(h, _lib.bp_set_checkpoint_interval(h, int(every)))
+
+
+def bp_set_grid(h, blocks):
+    _check(h, _lib.bp_set_grid(h, int(blocks)))
 
 
 def bp_set_persistent(h, mode):

@@ -778,6 +778,14 @@ bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
     return BP_OK;
 }
 
+bp_status bp_set_grid(bp_handle h, int blocks) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_grid: NULL handle");
+    h->err.clear();
+    if (blocks < 0 || blocks > (1 << 20)) return fail(h, BP_ERR_ARG, "bp_set_grid: blocks out of range");
+    h->blocks_override = blocks;
+    return BP_OK;
+}
+
 bp_status bp_set_persistent(bp_handle h, int mode) {
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_persistent: NULL handle");
     h->err.clear();
