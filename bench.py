@@ -244,7 +244,7 @@ def run_ours(args, cfg, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    out = {"elapsed": elapsed, "units": units_all, "launches": launches,
+    out = {"elapsed": elapsed, "units": units_all, "launches": launches, "layout": bp.bp_get_layout(G.h),
            "band_launch_s": band_s / (args.steps * K), "clocks": clk.summary()}
 
     # end to end through the public API: every step uploads its unary from
@@ -354,7 +354,7 @@ def run_batch_workload(args):
         torch.cuda.synchronize()
         b = bp.bp_batch_create(descs, dtype, stream=stream)
         del keep
-        tune_ms = bp.bp_batch_autotune(b, mode, 3)
+        tune_ms = bp.bp_batch_autotune(b, mode, 8)
         fam, tile = bp.bp_batch_get_tiling(b)
 
         def step():
@@ -695,10 +695,12 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * res["elapsed"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
-            "roofline": {"bound": "hbm", "kernel": "band_sum_kernel<32,1,4>", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": f"band_sum_kernel<{res['layout'][0]},{res['layout'][1]},{cfg.T}>",
+                         "achieved": achieved,
                          "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                          "peak_source": pk["source"], "algorithmic_bytes_per_launch": per_launch_bytes,
-                         "traffic": recorded_traffic("band_sum_kernel<32,1,4>", cfg)},
+                         "traffic": recorded_traffic(f"band_sum_kernel<{res['layout'][0]},{res['layout'][1]},{cfg.T}>",
+                                                     cfg)},
             "clocks": res["clocks"], "gpu_launches": res["launches"]}
     if "e2e" in res:
         line["e2e"] = res["e2e"]

@@ -335,7 +335,12 @@ bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_h
     h->W = W; h->H = H; h->M = M; h->Mp = Mp; h->dtype = dtype;
     h->dims = GridDims{W, H, M, Mp, (long long)W * H * Mp};
     Layout lays[8];
-    h->layout = layouts_for(Mp, lays, 8) > 0 ? lays[0] : Layout{32, 1};
+    const int nlay = std::min(8, layouts_for(Mp, lays, 8));
+    h->layout = nlay > 0 ? lays[0] : Layout{32, 1};
+    // the adjoint kernel holds more state per label: it keeps one chunk per lane
+    h->adj_layout = h->layout;
+    for (int i = 0; i < nlay; ++i)
+        if (lays[i].C == 1) h->adj_layout = lays[i];
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { bp_status st = cuda_fail(nullptr, e, "cudaGetDevice"); delete h; return st; }
     if (cuda_stream) {
@@ -570,6 +575,7 @@ bp_status bp_set_layout(bp_handle h, int L, int C) {
     for (int i = 0; i < n; ++i)
         if (lays[i].L == L && lays[i].C == C) {
             h->layout = lays[i];
+            h->adj_layout = lays[i];
             if (h->have_potential) h->fast = h->Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, h->Teff);
             return BP_OK;
         }

@@ -83,7 +83,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
     const int K = h->rec_iters, c = h->rec_every, Teff = h->Teff, NP = 2 * Teff + 2;
     const size_t sb = bpg_state_bytes(h);
     const long long nodes = (long long)h->W * h->H;
-    const int blocks = adjoint_blocks(h->dims, h->layout, Teff);
+    const int blocks = adjoint_blocks(h->dims, h->adj_layout, Teff);
     if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: no adjoint kernel for this layout");
     const int seg_states = c > 1 ? c - 1 : 1;
     if (h->seg_cap < seg_states) {
@@ -131,7 +131,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
             a.T = Teff;
             for (int i = 0; i < 2 * Teff + 1; ++i) a.w[i] = h->wf[i];
             a.fbar = h->fbarf;
-            BK_CK(h, launch_band_log_adjoint(a, h->layout, blocks, h->stream));
+            BK_CK(h, launch_band_log_adjoint(a, h->adj_layout, blocks, h->stream));
             h->launches += 1;
             ca ^= 1;
         }
