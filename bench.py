@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid1280x720_m128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-throughput", action="store_true",
+                    help="skip the FP32 O(mM) vs O(M^2) comparison on the host cores")
     ap.add_argument("--no-baselines", action="store_true", help="skip the O(M^2) baselines")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--persistent", type=int, default=-1, choices=[-1, 0, 1],
@@ -169,6 +171,39 @@ def oracle_sample(cfg, stereo_obj, target_s=10.0):
     rows = int(max(2, min(cfg.H, rows * target_s / max(t, 1e-3))))
     t, u = run(rows)
     return u / t, f"1 synchronous iteration on rows 0..{rows - 1} ({cfg.W}x{rows} grid) of the workload", t
+
+
+def cpu_throughput_sample(cfg, stereo_obj, rows=180, reps=3):
+    """Sec. 6's CPU comparison on this machine's host cores: one FP32
+    synchronous iteration of the O(mM) update (Eq. 7) and of the O(M^2)
+    update (Eq. 2), OpenMP over rows, on the first `rows` rows of the
+    workload (median of `reps` after one warm-up)."""
+    import cpu_baselines as cb
+    from oracle import stereo
+    R = max(2, min(rows, cfg.H))
+    g = np.ascontiguousarray(wl.unary_f32(stereo_obj)[:R])
+    tab, fbar = wl.pair_table_f32(cfg.alpha, cfg.T)
+    F = stereo.compatibility_matrix(tab.astype(np.float64), cfg.T, fbar, cfg.M).astype(np.float32)
+    pin = np.full((4, R, cfg.W, cfg.M), 1.0 / cfg.M, np.float32)
+    pout = np.empty_like(pin)
+    units = wl.directed_edges(cfg.W, R) * cfg.M
+
+    def timed(fn):
+        ts = []
+        for i in range(reps + 1):
+            t0 = time.perf_counter()
+            fn()
+            if i:
+                ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+
+    tb = timed(lambda: cb.band_iteration(g, pin, pout, tab, cfg.T, fbar))
+    td = timed(lambda: cb.dense_iteration(g, pin, pout, F))
+    return {"band_mM": {"value": units / tb, "unit": UNIT, "ms_per_iter": 1e3 * tb},
+            "dense_M2": {"value": units / td, "unit": UNIT, "ms_per_iter": 1e3 * td},
+            "speedup": td / tb, "cores": cb.threads(), "dtype": "f32",
+            "sample": f"1 synchronous iteration on rows 0..{R - 1} ({cfg.W}x{R} grid) of the workload, "
+                      f"median of {reps}"}
 
 
 # ------------------------------------------------------------------ GPU arm ----
@@ -710,6 +745,8 @@ def main():
         st = wl.make_stereo(cfg)
         v, desc, t = oracle_sample(cfg, st, target_s=10.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if not args.no_cpu_throughput:
+        line["cpu_throughput"] = cpu_throughput_sample(cfg, wl.make_stereo(cfg))
     print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -173,9 +173,12 @@ void bp_destroy(bp_handle h);
 
 /* ---- tuning ---------------------------------------------------------------
  * The O(mM) kernel assigns L lanes to a node, each lane holding V = 4C
- * consecutive labels (L * 4C = padded label count).  bp_set_layout picks
- * (L, C); bp_autotune times every layout available for the handle's
- * (M, T, mode) and keeps the fastest. */
+ * consecutive labels (L * 4C = padded label count).  The log-domain kernels
+ * (BP_LOG iterations, the recorded forward and its adjoint) keep a layout of
+ * their own, by default one chunk per lane.  bp_set_layout sets (L, C) for
+ * both; bp_get_layout reports the plain-mode layout; bp_autotune times every
+ * layout available for the handle's (M, T, mode) and keeps the fastest for
+ * the layout that mode uses (the log-domain one when mode has BP_LOG). */
 bp_status bp_set_layout(bp_handle h, int lanes_per_node, int vec_chunks);
 bp_status bp_get_layout(bp_handle h, int *lanes_per_node, int *vec_chunks);
 bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms);

@@ -163,7 +163,7 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
             a.d = h->dims; a.parity = parity; a.T = h->Teff;
             for (int i = 0; i < 2 * h->Teff + 1; ++i) a.w[i] = h->wf[i];
             a.fbar = h->fbarf;
-            e = is_log ? launch_band_log(a, h->layout, h->blocks_override, h->stream)
+            e = is_log ? launch_band_log(a, h->log_layout, h->blocks_override, h->stream)
                        : launch_band_sum(a, h->layout, h->blocks_override, h->stream);
         } else {
             if (is_log) return cudaErrorNotSupported;
@@ -282,7 +282,8 @@ static bp_status run_iterations(bp_ctx *h, int n, int mode, int sched) {
         }
         return BP_OK;
     }
-    const GraphKey key{n, mode, sched, h->cur, h->layout.L, h->layout.C, h->blocks_override, persist ? 1 : 0};
+    const Layout &lay = (mode & BP_LOG) ? h->log_layout : h->layout;
+    const GraphKey key{n, mode, sched, h->cur, lay.L, lay.C, h->blocks_override, persist ? 1 : 0};
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -337,10 +338,12 @@ bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_h
     Layout lays[8];
     const int nlay = std::min(8, layouts_for(Mp, lays, 8));
     h->layout = nlay > 0 ? lays[0] : Layout{32, 1};
-    // the adjoint kernel holds more state per label: it keeps one chunk per lane
-    h->adj_layout = h->layout;
+    // the log-domain kernels (an exp per h entry, a log per output, and the
+    // adjoint's extra state per label) keep one chunk per lane: the same
+    // rounding path for the recorded forward and its adjoint
+    h->log_layout = h->layout;
     for (int i = 0; i < nlay; ++i)
-        if (lays[i].C == 1) h->adj_layout = lays[i];
+        if (lays[i].C == 1) h->log_layout = lays[i];
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { bp_status st = cuda_fail(nullptr, e, "cudaGetDevice"); delete h; return st; }
     if (cuda_stream) {
@@ -575,7 +578,7 @@ bp_status bp_set_layout(bp_handle h, int L, int C) {
     for (int i = 0; i < n; ++i)
         if (lays[i].L == L && lays[i].C == C) {
             h->layout = lays[i];
-            h->adj_layout = lays[i];
+            h->log_layout = lays[i];
             if (h->have_potential) h->fast = h->Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, h->Teff);
             return BP_OK;
         }
@@ -746,7 +749,8 @@ bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
     if (bp_status st = ensure_buffer(h, &h->tune_buf, bpg_state_bytes(h), "autotune buffer")) return st;
     Layout lays[8];
     const int n = std::min(8, layouts_for(h->Mp, lays, 8));
-    const Layout saved = h->layout;
+    Layout &target = is_log ? h->log_layout : h->layout;
+    const Layout saved = target;
     const int saved_cur = h->cur;
     BP_CK(h, cudaMemcpyAsync(h->tune_buf, h->msg[h->cur], bpg_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
     cudaEvent_t e0, e1;
@@ -757,7 +761,7 @@ bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
     const int md = mode & (BP_MAX | BP_LOG);
     for (int i = 0; i < n; ++i) {
         if (h->Teff > kTMaxFast || !band_fast_available(h->Mp, lays[i], h->Teff)) continue;
-        h->layout = lays[i];
+        target = lays[i];
         h->fast = true;
         bp_status st = run_iterations(h, n_iters, md, BP_SYNC);        // warm
         if (!st) st = (cudaEventRecord(e0, h->stream) == cudaSuccess) ? BP_OK : BP_ERR_CUDA;
@@ -769,14 +773,15 @@ bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
         if (st) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            h->layout = saved;
+            target = saved;
+            h->fast = h->Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, h->Teff);
             return st == BP_ERR_CUDA ? fail(h, st, "bp_autotune: timing failed") : st;
         }
         if (ms < best) { best = ms; best_lay = lays[i]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->layout = best_lay;
+    target = best_lay;
     h->fast = h->Teff <= kTMaxFast && band_fast_available(h->Mp, h->layout, h->Teff);
     h->cur = saved_cur;
     BP_CK(h, cudaMemcpyAsync(h->msg[h->cur], h->tune_buf, bpg_state_bytes(h), cudaMemcpyDeviceToDevice, h->stream));

@@ -59,7 +59,7 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
     for (int t = 0; t < n_iters; ++t) {
         if (t % c == 0)
             BK_CK(h, cudaMemcpyAsync(h->ckpts[t / c], h->msg[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream));
-        BK_CK(h, launch_band_log(log_args(h, h->msg[h->cur], h->msg[h->cur ^ 1]), h->layout, h->blocks_override,
+        BK_CK(h, launch_band_log(log_args(h, h->msg[h->cur], h->msg[h->cur ^ 1]), h->log_layout, h->blocks_override,
                                  h->stream));
         h->cur ^= 1;
         h->launches += 1;
@@ -83,7 +83,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
     const int K = h->rec_iters, c = h->rec_every, Teff = h->Teff, NP = 2 * Teff + 2;
     const size_t sb = bpg_state_bytes(h);
     const long long nodes = (long long)h->W * h->H;
-    const int blocks = adjoint_blocks(h->dims, h->adj_layout, Teff);
+    const int blocks = adjoint_blocks(h->dims, h->log_layout, Teff);
     if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: no adjoint kernel for this layout");
     const int seg_states = c > 1 ? c - 1 : 1;
     if (h->seg_cap < seg_states) {
@@ -116,7 +116,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
         states[0] = h->ckpts[seg];
         for (int j = 1; j < len; ++j) {
             states[j] = (char *)h->seg_buf + (size_t)(j - 1) * sb;
-            BK_CK(h, launch_band_log(log_args(h, states[j - 1], states[j]), h->layout, h->blocks_override, h->stream));
+            BK_CK(h, launch_band_log(log_args(h, states[j - 1], states[j]), h->log_layout, h->blocks_override, h->stream));
             h->launches += 1;
         }
         for (int t = end - 1; t >= start; --t) {
@@ -131,7 +131,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
             a.T = Teff;
             for (int i = 0; i < 2 * Teff + 1; ++i) a.w[i] = h->wf[i];
             a.fbar = h->fbarf;
-            BK_CK(h, launch_band_log_adjoint(a, h->adj_layout, blocks, h->stream));
+            BK_CK(h, launch_band_log_adjoint(a, h->log_layout, blocks, h->stream));
             h->launches += 1;
             ca ^= 1;
         }

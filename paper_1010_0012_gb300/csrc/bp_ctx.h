@@ -61,7 +61,7 @@ struct bp_ctx {
     void *d_sp_rowptr = nullptr, *d_sp_cols = nullptr, *d_sp_w = nullptr;
 
     bpg::Layout layout{32, 1};
-    bpg::Layout adj_layout{32, 1};  // layout of the adjoint kernel (fewest labels per lane)
+    bpg::Layout log_layout{32, 1};  // layout of the log-domain forward and adjoint kernels
     bool fast = false;              // register/shuffle kernels serve (M, T)
     int blocks_override = 0;
     bool use_graphs = true;

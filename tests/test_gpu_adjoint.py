@@ -121,9 +121,7 @@ def test_ill_conditioned_beta_gradient_stays_at_the_fp32_floor():
     ~3400 times the result), so FP32 rounding carried through 30 iterations,
     not the method, sets its accuracy.  The bar there: the error stays below
     2^-24 * K * sum |dL/d log g * cost| (each per-node term accurate to K
-    rounding steps).  dL/d alpha is a cancelling sum on this crop too (its
-    terms sum_d dL/df(d) |d| f(d) are ~26 times the result), so alpha and fbar
-    are held to 1e-3 here; the 96 x 96 and 256 x 256 checks above keep 1e-4."""
+    rounding steps), with alpha and fbar still within 1e-4."""
     import dataclasses
     cfg = dataclasses.replace(wl.CONFIGS["grid256_m64_grad"], W=40, H=32)
     st = wl.make_stereo(cfg)
@@ -135,4 +133,4 @@ def test_ill_conditioned_beta_gradient_stays_at_the_fp32_floor():
     floor = 2.0 ** -24 * K * float(np.sum(np.abs(ref["d_logg"] * st.cost)))
     assert abs(gpu["d_beta"] - fd["d_beta"]) <= floor
     for k in ("d_alpha", "d_fbar"):
-        assert abs(gpu[k] - fd[k]) <= 1e-3 * max(1.0, abs(fd[k]))
+        assert abs(gpu[k] - fd[k]) <= GRAD_TOL * max(1.0, abs(fd[k]))
