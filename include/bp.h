@@ -221,7 +221,8 @@ bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const float *dev_unar
  * the inhomogeneous case of Sec. 1) advanced together by ONE persistent
  * cooperative kernel launch per bp_batch_iterate call, captured once in a CUDA
  * graph and replayed.  Synchronous schedule only; 2 <= M <= 256, band
- * half-width min(T, M-1) <= 8. */
+ * half-width min(T, M-1) <= 8.  Inside the launch, blocks take the work items
+ * (grouped by band width and label count) from a shared counter. */
 typedef struct {
     int W, H, M;               /* grid and label count of this MRF                 */
     int T;                     /* band half-width                                  */

@@ -3,11 +3,17 @@
 //
 // One cooperative launch runs every iteration of every MRF.  The nodes of all
 // MRFs are cut into work items (mrf, first node, node count) of roughly equal
-// bytes; block b takes items b, b + G, b + 2G, ... and, per item, runs the
-// per-node update (SumBand / MinBand) compiled for that MRF's padded label
-// count and band half-width.  Between iterations all blocks meet at a grid
-// barrier whose wait is bounded: on time-out the block records an error code
-// in the status word and the kernel returns (the host reports BP_ERR_TIMEOUT).
+// bytes, listed by (band half-width, label count) class.  Blocks take items
+// in list order from one 64-bit ticket counter (ticket k = item k % n_items of
+// step k / n_items), each block fetching its next ticket while it works on the
+// current item, and run per item the per-node update (SumBand / MinBand)
+// compiled for that MRF's padded label count and band half-width.  Taking the
+// list in order keeps the whole grid inside one class at a time, so an SM
+// runs one compiled variant at a time; taking it dynamically balances items
+// whose cost differs with T.  A ticket past the current step is kept for the
+// step it belongs to.  Between iterations all blocks meet at a grid barrier
+// whose wait is bounded: on time-out the block records an error code in the
+// status word and the kernel returns (the host reports BP_ERR_TIMEOUT).
 // Messages written by other blocks are read with L2-coherent loads.
 #pragma once
 
@@ -159,14 +165,27 @@ __device__ __forceinline__ void batch_dispatch(const BatchMrf *__restrict__ m, i
 // separately so that the synchronous batch kernel keeps its registers.
 template <int FAM, bool MIN, bool RB>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
+    __shared__ unsigned long long s_ticket[2];
     const int phases = RB ? 2 : 1;
     const int total = a.n_iters * phases;
+    const unsigned long long n_items = (unsigned long long)a.n_items;
+    // thread 0 writes slot `slot ^ 1` while the others read slot `slot`; a
+    // slot is rewritten only after the __syncthreads that follows its read
+    int slot = 0;
+    if (threadIdx.x == 0) s_ticket[0] = atomicAdd(a.tickets, 1ull);
+    __syncthreads();
+    unsigned long long ticket = s_ticket[0];
     for (int step = 0; step < total; ++step) {
         const int parity = RB ? (step & 1) : -1;
         const int src = RB ? a.start_buf : ((a.start_buf + step) & 1);
-        for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-            const BatchItem item = a.items[it];
+        const unsigned long long first = (unsigned long long)step * n_items;
+        while (ticket < first + n_items) {
+            if (threadIdx.x == 0) s_ticket[slot ^ 1] = atomicAdd(a.tickets, 1ull);
+            const BatchItem item = a.items[ticket - first];
             batch_dispatch<FAM, MIN, RB>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
+            __syncthreads();
+            slot ^= 1;
+            ticket = s_ticket[slot];
         }
         if (step + 1 < total) {
             if (!batch_grid_barrier(a.bar_count, a.bar_gen, gridDim.x + a.extra_arrivals, a.limit_ns, a.status))

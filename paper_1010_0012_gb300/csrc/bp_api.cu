@@ -210,7 +210,7 @@ static bp_status persistent_setup(bp_ctx *h) {
         m.zero_min = bpg_zero_min(h->wi) ? 1 : 0;
     }
     if (bp_status st = ensure_buffer(h, &h->p_mrf, sizeof(BatchMrf), "persistent descriptor")) return st;
-    if (bp_status st = ensure_buffer(h, &h->p_bar, 2 * sizeof(unsigned), "barrier words")) return st;
+    if (bp_status st = ensure_buffer(h, &h->p_bar, kBatchCtlWords * sizeof(unsigned), "barrier words")) return st;
     const int maxb = h->dtype == BP_I32 ? std::max(batch_max_blocks_min(1, false), batch_max_blocks_min(1, true))
                                         : std::max(batch_max_blocks_sum(1, false), batch_max_blocks_sum(1, true));
     const int gpb = kBlock / batch_lanes_per_node(1, h->Mp);
@@ -230,7 +230,7 @@ static bp_status persistent_setup(bp_ctx *h) {
         BP_CK(h, cudaStreamSynchronize(h->stream));   // the host vector dies here
     }
     BP_CK(h, cudaMemcpyAsync(h->p_mrf, &m, sizeof(BatchMrf), cudaMemcpyHostToDevice, h->stream));
-    BP_CK(h, cudaMemsetAsync(h->p_bar, 0, 2 * sizeof(unsigned), h->stream));
+    BP_CK(h, cudaMemsetAsync(h->p_bar, 0, kBatchCtlWords * sizeof(unsigned), h->stream));
     BP_CK(h, cudaStreamSynchronize(h->stream));
     h->p_ready = true;
     return BP_OK;
@@ -245,11 +245,12 @@ static cudaError_t issue_persistent(bp_ctx *h, int n, int sched, int cur) {
     a.start_buf = cur;
     a.redblack = sched == BP_REDBLACK ? 1 : 0;
     a.bar_count = (unsigned *)h->p_bar;
-    a.bar_gen = (unsigned *)h->p_bar + 1;
+    a.bar_gen = (unsigned *)h->p_bar + kBatchGenWord;
+    a.tickets = reinterpret_cast<unsigned long long *>((unsigned *)h->p_bar + kBatchTicketWord);
     a.extra_arrivals = 0;
     a.limit_ns = 2000000000ull;
     a.status = h->d_status;
-    cudaError_t e = cudaMemsetAsync(h->p_bar, 0, sizeof(unsigned), h->stream);
+    cudaError_t e = cudaMemsetAsync(h->p_bar, 0, kBatchZeroBytes, h->stream);   // arrivals, ticket counter
     if (e != cudaSuccess) return e;
     const bool rb = sched == BP_REDBLACK;
     const int maxb = h->dtype == BP_I32 ? batch_max_blocks_min(1, rb) : batch_max_blocks_sum(1, rb);

@@ -65,7 +65,7 @@ struct bp_batch_ctx {
     BatchMrf *d_mrfs = nullptr;
     BatchItem *d_items = nullptr;
     int n_items = 0, items_cap = 0;
-    unsigned *d_bar = nullptr;   // [count, generation]
+    unsigned *d_bar = nullptr;   // barrier and work-counter words (kBatchCtlWords)
     int *d_status = nullptr;
     int family = 1;
     int tile_words = 16384;
@@ -98,10 +98,18 @@ static void clear_batch_graphs(bp_batch b) {
     b->graphs.clear();
 }
 
-// Cut every MRF into items of about `tile_words` label words, whole groups of nodes.
+// Cut every MRF into items of about `tile_words` label words, whole groups of
+// nodes, listed class by class: widest band first, then most labels (one
+// compiled variant of the kernel per class).
 static bp_status build_items(bp_batch b) {
+    std::vector<int> order(b->n);
+    for (int k = 0; k < b->n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const MrfHost &p = b->mrfs[x], &q = b->mrfs[y];
+        return std::make_pair(p.Teff, p.Mp) > std::make_pair(q.Teff, q.Mp);
+    });
     std::vector<BatchItem> items;
-    for (int k = 0; k < b->n; ++k) {
+    for (int k : order) {
         const MrfHost &m = b->mrfs[k];
         const int gpb = kBlock / batch_lanes_per_node(b->family, m.Mp);
         int tile = std::max(gpb, (b->tile_words / m.Mp) / gpb * gpb);
@@ -136,11 +144,13 @@ static cudaError_t issue_batch(bp_batch b, int n_iters, int cur) {
     a.n_iters = n_iters;
     a.start_buf = cur;
     a.bar_count = b->d_bar;
-    a.bar_gen = b->d_bar + 1;
+    a.bar_gen = b->d_bar + kBatchGenWord;
+    a.tickets = reinterpret_cast<unsigned long long *>(b->d_bar + kBatchTicketWord);
     a.extra_arrivals = b->extra_arrivals;
     a.limit_ns = b->limit_ns;
     a.status = b->d_status;
-    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned), b->stream);   // arrivals start at 0
+    // arrivals and the ticket counter start at 0
+    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, kBatchZeroBytes, b->stream);
     if (e != cudaSuccess) return e;
     const int blocks = batch_blocks(b);
     return b->dtype == BP_I32 ? launch_batch_min(a, b->family, blocks, b->stream)
@@ -277,7 +287,7 @@ bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void 
     }
     if (st == BP_OK) {
         if (cudaMalloc(&b->d_mrfs, n * sizeof(BatchMrf)) != cudaSuccess ||
-            cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
+            cudaMalloc(&b->d_bar, kBatchCtlWords * sizeof(unsigned)) != cudaSuccess ||
             cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();
             st = bfail(nullptr, BP_ERR_OOM, "bp_batch_create: device allocation failed");
@@ -285,7 +295,7 @@ bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void 
     }
     if (st == BP_OK) {
         if (cudaMemcpyAsync(b->d_mrfs, dm.data(), n * sizeof(BatchMrf), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-            cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream) != cudaSuccess ||
+            cudaMemsetAsync(b->d_bar, 0, kBatchCtlWords * sizeof(unsigned), b->stream) != cudaSuccess ||
             cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess ||
             cudaStreamSynchronize(b->stream) != cudaSuccess)
             st = bfail(nullptr, BP_ERR_CUDA, "bp_batch_create: descriptor upload failed");
@@ -457,7 +467,7 @@ bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_
             }
     }
     const int fams[] = {1, 2};
-    const int tiles[] = {4096, 16384, 65536};
+    const int tiles[] = {16384, 65536, 262144};
     cudaEvent_t e0, e1;
     BB_CK(b, cudaEventCreate(&e0));
     BB_CK(b, cudaEventCreate(&e1));

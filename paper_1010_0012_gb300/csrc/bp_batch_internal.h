@@ -39,10 +39,19 @@ struct BatchArgs {
     int redblack;               // 1: two in-place half-steps per iteration on msg[start_buf]
     unsigned *bar_count;        // grid barrier: arrivals, generation
     unsigned *bar_gen;
+    unsigned long long *tickets;   // work counter, zero at launch: ticket k is item k % n_items of step k / n_items
     int extra_arrivals;         // 0; > 0 makes the barrier wait for blocks that never come
     unsigned long long limit_ns;
     int *status;
 };
+
+// Layout of the barrier / work-counter words (32 bytes, 8-byte aligned):
+// [0] barrier arrivals, [2..3] the 64-bit ticket counter (both zeroed before
+// every launch: kBatchZeroBytes from the start), [4] barrier generation.
+constexpr int kBatchCtlWords = 8;
+constexpr size_t kBatchZeroBytes = 16;
+constexpr int kBatchTicketWord = 2;
+constexpr int kBatchGenWord = 4;
 
 // Launch one persistent cooperative batch kernel (family 1 or 2).
 cudaError_t launch_batch(const BatchArgs &a, int family, bool min_sum, int blocks, cudaStream_t s);
