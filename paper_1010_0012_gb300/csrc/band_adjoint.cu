@@ -12,6 +12,8 @@
 //   dw(d)    += sum_{x_j} nu(x_j) h(x_j + d)                           (= dL/df(d))
 //   dfbar    += S sum_x nu(x) - sum_d dw(d)   (fbar enters u directly and through w)
 // The common factor exp(A) of h, u, Z and nu cancels in every product above.
+// h is recomputed exactly as the forward kernel computes it; delta / u uses
+// the hardware approximate division (2 ulp; u > 0 is a normal float here).
 //
 // One kernel launch reverses one synchronous iteration for every node; the
 // per-block sums of dw and dfbar go to a scratch row per (iteration, block),
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
             float S = 0.f, Z = 0.f;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                h[k] = lab_ok[k] ? expf(h[k] - amax) : 0.f;
+                h[k] = lab_ok[k] ? expf(h[k] - amax) : 0.f;   // as the forward kernel
                 S += h[k];
                 Z = fmaf(h[k], cz[k], Z);
             }
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
                 float u = fbar * S;
 #pragma unroll
                 for (int d = -T; d <= T; ++d) u = fmaf(w[d + T], win[T + k + d], u);
-                nu[k] = lab_ok[k] ? del[k] / u - nd * invZ : 0.f;
+                nu[k] = lab_ok[k] ? __fdividef(del[k], u) - nd * invZ : 0.f;
                 nn += nu[k];
             }
             nn = group_sum<L>(nn);

@@ -6,6 +6,12 @@
 // forms the four products h of Eq. 5 in registers, and writes the four outgoing
 // messages (4 x Mp words) straight into the neighbours' incoming planes:
 //
+// The log-domain form (messages and unary stored as natural logs) takes h from
+// exp(log g + sum of log-messages - their maximum) and stores log m.  The log
+// is the hardware approximation __logf (absolute error about 2^-21 near 1,
+// a few ulp elsewhere); the exp stays the full-precision expf, because the
+// error of __expf grows with |x| and shows in ill-conditioned gradients.
+//
 //   sum-product (Eq. 7):
 //     S      = sum_x h(x)                        (group shuffle reduction)
 //     B(x_j) = sum_{|d| <= T} [f(d) - fbar] h(x_j + d)   (band; halo via shuffles)
@@ -65,6 +71,16 @@ template <int V, typename T>
 __device__ __forceinline__ void fill_vec(T (&v)[V], T x) {
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = x;
+}
+
+// minimum of a register vector, three-input DPX minimum where it pairs up
+template <int V>
+__device__ __forceinline__ int32_t min_vec(const int32_t (&v)[V]) {
+    int32_t r = v[0];
+#pragma unroll
+    for (int k = 1; k + 1 < V; k += 2) r = __vimin3_s32(r, v[k], v[k + 1]);
+    if (V % 2 == 0) r = min(r, v[V - 1]);
+    return r;
 }
 
 // ------------------------------------------------------- group reductions ----
@@ -271,7 +287,7 @@ struct SumBand {
 #pragma unroll
                 for (int d = -T; d <= T; ++d) acc = fmaf(w[d + T], win[T + k + d], acc);
                 const float mv = fmaf(acc, inv, base_term);
-                o[k] = lab_ok[k] ? (LOG ? logf(mv) : mv) : 0.f;
+                o[k] = lab_ok[k] ? (LOG ? __logf(mv) : mv) : 0.f;
             }
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
         }
@@ -333,7 +349,6 @@ struct MinBand {
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             int32_t h[V];
-            int32_t hmin = kIntBig;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 int32_t s = ev[k];
@@ -341,24 +356,23 @@ struct MinBand {
                 for (int u = 0; u < 4; ++u)
                     if (u != t) s += m[u][k];
                 h[k] = lab_ok[k] ? s : kIntBig;
-                hmin = min(hmin, h[k]);
             }
+            int32_t hmin = min_vec<V>(h);
             hmin = group_min<L>(hmin);
 
             int32_t win[V + 2 * T];
             band_window<L, V, T, int32_t>(win, h, q, kIntBig);
             const int32_t flat = ebar + hmin;
             int32_t u[V];
-            int32_t umin = kIntBig;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
+                // min(E(d) + h(x + d), running min) in one DPX add-min per band term
                 int32_t b = flat;
 #pragma unroll
-                for (int d = -T; d <= T; ++d) b = min(b, w[d + T] + win[T + k + d]);
+                for (int d = -T; d <= T; ++d) b = __viaddmin_s32(w[d + T], win[T + k + d], b);
                 u[k] = lab_ok[k] ? b : kIntBig;
-                umin = min(umin, u[k]);
             }
-            umin = zero_min ? w[T] + hmin : group_min<L>(umin);
+            const int32_t umin = zero_min ? w[T] + hmin : group_min<L>(min_vec<V>(u));
 #pragma unroll
             for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, u);
