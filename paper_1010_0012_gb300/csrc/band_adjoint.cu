@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
             float S = 0.f, Z = 0.f;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                h[k] = lab_ok[k] ? expf(h[k] - amax) : 0.f;   // as the forward kernel
+                h[k] = lab_ok[k] ? exp_shifted(h[k] - amax) : 0.f;   // as the forward kernel
                 S += h[k];
                 Z = fmaf(h[k], cz[k], Z);
             }

@@ -9,8 +9,9 @@
 // The log-domain form (messages and unary stored as natural logs) takes h from
 // exp(log g + sum of log-messages - their maximum) and stores log m.  The log
 // is the hardware approximation __logf (absolute error about 2^-21 near 1,
-// a few ulp elsewhere); the exp stays the full-precision expf, because the
-// error of __expf grows with |x| and shows in ill-conditioned gradients.
+// a few ulp elsewhere); the exp is exp_shifted below, accurate to a few ulp
+// over the whole range (the error of __expf grows with |x|, which shows in
+// ill-conditioned gradients).
 //
 //   sum-product (Eq. 7):
 //     S      = sum_x h(x)                        (group shuffle reduction)
@@ -81,6 +82,24 @@ __device__ __forceinline__ int32_t min_vec(const int32_t (&v)[V]) {
     for (int k = 1; k + 1 < V; k += 2) r = __vimin3_s32(r, v[k], v[k + 1]);
     if (V % 2 == 0) r = min(r, v[V - 1]);
     return r;
+}
+
+// e^x for x <= 0 (the max-shifted exponents of the log-domain kernels) within a
+// few ulp.  x log2(e) is split exactly into head + tail (the FMA TwoProduct of
+// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 2005, plus the tail of the
+// constant log2(e) itself); the head goes to the hardware 2^y
+// (ex2.approx.ftz, a 2-ulp approximation whose input is now exact), the tail
+// to the first-order factor 1 + tail ln 2.  Results below 2^-126 flush to 0.
+__device__ __forceinline__ float exp_shifted(float x) {
+    constexpr float kLog2eHi = 1.44269502162933349609375f;   // nearest float to log2(e)
+    constexpr float kLog2eLo = 1.9259629911266175e-08f;      // log2(e) - kLog2eHi
+    constexpr float kLn2 = 0.693147180559945309f;
+    const float hi = x * kLog2eHi;
+    float lo = fmaf(x, kLog2eHi, -hi);
+    lo = fmaf(x, kLog2eLo, lo);
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(hi));
+    return fmaf(r, lo * kLn2, r);
 }
 
 // ------------------------------------------------------- group reductions ----
@@ -264,7 +283,7 @@ struct SumBand {
                 }
                 amax = group_max<L>(amax);
 #pragma unroll
-                for (int k = 0; k < V; ++k) h[k] = lab_ok[k] ? expf(h[k] - amax) : 0.f;
+                for (int k = 0; k < V; ++k) h[k] = lab_ok[k] ? exp_shifted(h[k] - amax) : 0.f;
             }
 
             float S = 0.f, Z = 0.f;
