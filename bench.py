@@ -559,6 +559,9 @@ def run_sparse_workload(args):
     import torch
     from paper_1010_0012_gb300 import bp
     cfg = wl.CONFIGS["grid1280x720_m128"]
+    if args.rows:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, H=min(args.rows, cfg.H))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     st = wl.make_stereo(cfg)
     rng = np.random.default_rng(7)
@@ -601,7 +604,8 @@ def run_sparse_workload(args):
     line = {"metric": METRIC + " (general sparse compatibility, 9 pairs per label)",
             "value": res["sum_f32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1280x720, M=128, random non-difference pattern, 10 synchronous iterations"},
+            "config": {"workload": f"{cfg.W}x{cfg.H}, M={cfg.M}, random non-difference pattern, 10 synchronous "
+                                   "iterations"},
             "modes": res}
     print(json.dumps(line))
 

@@ -106,8 +106,9 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
  * fbar (Ebar).  host_rowptr has M+1 entries, rowptr[0] = 0.  One message then
  * costs O(nnz) with nnz = rowptr[M] (O(mM) for m pairs per label).  Replaces
  * any band potential; BP_ERR_POTENTIAL in max mode if some E > Ebar;
- * BP_ERR_ARG if the pattern does not fit the kernel's shared memory (about
- * 25,000 pairs at M = 128).  Log mode and bp_backward need a band potential. */
+ * BP_ERR_UNSUPPORTED for M > 512.  The pattern is copied to the device (8
+ * bytes per receiver label per entry of the longest list).  Log mode and
+ * bp_backward need a band potential. */
 bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
                                   const void *host_vals, double fbar);
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <tuple>
@@ -126,16 +127,13 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
         cudaError_t e;
         if (h->sparse) {
             if (is_log) return cudaErrorNotSupported;
-            const int nnz = (int)h->sp_cols.size();
             if (h->dtype == BP_I32) {
                 SparseArgsI a{(const int32_t *)h->unary, (const int32_t *)in, (int32_t *)out, h->dims, parity,
-                              (const int32_t *)h->d_sp_rowptr, (const int32_t *)h->d_sp_cols,
-                              (const int32_t *)h->d_sp_w, nnz, h->ebar};
+                              (const int32_t *)h->d_sp_len, (const int2 *)h->d_sp_ell, h->ebar};
                 e = launch_sparse_min(a, h->stream);
             } else {
                 SparseArgsF a{(const float *)h->unary, (const float *)in, (float *)out, h->dims, parity,
-                              (const int32_t *)h->d_sp_rowptr, (const int32_t *)h->d_sp_cols,
-                              (const float *)h->d_sp_w, nnz, h->fbarf};
+                              (const int32_t *)h->d_sp_len, (const int2 *)h->d_sp_ell, h->fbarf};
                 e = launch_sparse_sum(a, h->stream);
             }
             if (e != cudaSuccess) return e;
@@ -380,7 +378,7 @@ void bp_destroy(bp_handle h) {
     clear_graphs(h);
     bpg_free_extras(h);
     void *bufs[] = {h->unary, h->log_unary, h->msg[0], h->msg[1], h->d_wf, h->d_wi, h->d_dense, h->d_status,
-                    h->tune_buf, h->d_sp_rowptr, h->d_sp_cols, h->d_sp_w};
+                    h->tune_buf, h->d_sp_len, h->d_sp_ell};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -484,6 +482,63 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
     return BP_OK;
 }
 
+// Order of each receiver label's pattern entries for the sparse kernels: the
+// eight lanes of a quarter-warp (receiver labels 8q .. 8q + 7) gather, at
+// step i, their i-th entries with 16-byte loads, which conflict when two
+// lanes hit the same 16-byte bank group (slot mod 8) at different slots.  At
+// every step a maximum matching of lanes to bank groups (augmenting paths)
+// picks conflict-free entries for as many lanes as possible; the others take
+// their next entry.  Returns, for each CSR position, the CSR index to use.
+static std::vector<int> sparse_bank_order(int M, const int32_t *rowptr, const int32_t *cols) {
+    std::vector<int> order(rowptr[M]);
+    for (int b = 0; b < M; b += 8) {
+        const int nl = std::min(8, M - b);
+        std::vector<std::vector<int>> rem(nl);
+        for (int l = 0; l < nl; ++l)
+            for (int p = rowptr[b + l]; p < rowptr[b + l + 1]; ++p) rem[l].push_back(p);
+        std::vector<int> filled(nl, 0);
+        auto group = [&](int p) { return sp_label_slot(cols[p]) & 7; };
+        for (;;) {
+            bool any = false;
+            for (int l = 0; l < nl; ++l) any = any || !rem[l].empty();
+            if (!any) break;
+            int owner[8];
+            std::fill(owner, owner + 8, -1);
+            std::vector<int> pick(nl, -1);   // index into rem[l]
+            std::function<bool(int, unsigned &)> augment = [&](int l, unsigned &seen) -> bool {
+                for (int j = 0; j < (int)rem[l].size(); ++j) {
+                    const int g = group(rem[l][j]);
+                    if (seen & (1u << g)) continue;
+                    seen |= 1u << g;
+                    if (owner[g] < 0 || augment(owner[g], seen)) {
+                        owner[g] = l;
+                        pick[l] = j;
+                        return true;
+                    }
+                }
+                return false;
+            };
+            std::vector<int> lanes;
+            for (int l = 0; l < nl; ++l)
+                if (!rem[l].empty()) lanes.push_back(l);
+            std::stable_sort(lanes.begin(), lanes.end(), [&](int x, int y) { return rem[x].size() > rem[y].size(); });
+            for (int l : lanes) {
+                unsigned seen = 0;
+                augment(l, seen);
+            }
+            for (int l : lanes) {
+                // a lane whose group was taken over during augmentation keeps
+                // its entry in that group only if it still owns it
+                int j = pick[l];
+                if (j < 0 || owner[group(rem[l][j])] != l) j = 0;
+                order[rowptr[b + l] + filled[l]++] = rem[l][j];
+                rem[l].erase(rem[l].begin() + j);
+            }
+        }
+    }
+    return order;
+}
+
 bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
                                   const void *host_vals, double fbar) {
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_potential_sparse: NULL handle");
@@ -495,8 +550,7 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
     for (int x = 0; x < h->M; ++x)
         if (host_rowptr[x + 1] < host_rowptr[x]) return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: rowptr decreases");
     const int nnz = host_rowptr[h->M];
-    if (sparse_smem_bytes(h->M, h->Mp, nnz) > 220 * 1024)
-        return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: too many compatible pairs for shared memory");
+    if (h->Mp > 512) return fail(h, BP_ERR_UNSUPPORTED, "bp_set_potential_sparse: serves M <= 512");
     std::vector<char> seen(h->M, 0);
     for (int xj = 0; xj < h->M; ++xj) {
         for (int p = host_rowptr[xj]; p < host_rowptr[xj + 1]; ++p) {
@@ -507,8 +561,7 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
         }
         for (int p = host_rowptr[xj]; p < host_rowptr[xj + 1]; ++p) seen[host_cols[p]] = 0;
     }
-    std::vector<float> wf;
-    std::vector<int32_t> wi;
+    std::vector<int32_t> wbits(nnz);   // per entry: f - fbar (float bits) or E
     if (h->dtype == BP_F32) {
         const float *v = (const float *)host_vals;
         for (int p = 0; p < nnz; ++p)
@@ -516,7 +569,10 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
                 return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: values must be finite and >= 0");
         h->sp_valf.assign(v, v + nnz);
         h->fbarf = (float)fbar;
-        for (int p = 0; p < nnz; ++p) wf.push_back((float)((double)v[p] - (double)h->fbarf));
+        for (int p = 0; p < nnz; ++p) {
+            const float w = (float)((double)v[p] - (double)h->fbarf);
+            std::memcpy(&wbits[p], &w, 4);
+        }
     } else {
         if (fbar != std::floor(fbar) || fbar >= (double)(1 << 26))
             return fail(h, BP_ERR_ARG, "bp_set_potential_sparse: Ebar must be an integer in [0, 2^26)");
@@ -529,25 +585,35 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
         }
         h->sp_vali.assign(v, v + nnz);
         h->ebar = (int32_t)fbar;
-        wi.assign(v, v + nnz);
+        std::memcpy(wbits.data(), v, (size_t)nnz * 4);
     }
     h->sp_rowptr.assign(host_rowptr, host_rowptr + h->M + 1);
     h->sp_cols.assign(host_cols, host_cols + nnz);
-    void *bufs[] = {h->d_sp_rowptr, h->d_sp_cols, h->d_sp_w};
+    // interleave by receiver label (entry i of x_j at i * M + x_j), sender
+    // labels replaced by their shared-memory slots, entries ordered per
+    // quarter-warp against bank conflicts
+    int rmax = 1;
+    std::vector<int32_t> len(h->M);
+    for (int xj = 0; xj < h->M; ++xj) {
+        len[xj] = host_rowptr[xj + 1] - host_rowptr[xj];
+        rmax = std::max(rmax, len[xj]);
+    }
+    const std::vector<int> order = sparse_bank_order(h->M, host_rowptr, host_cols);
+    std::vector<int32_t> ell((size_t)rmax * h->M * 2, 0);
+    for (int xj = 0; xj < h->M; ++xj)
+        for (int i = 0; i < len[xj]; ++i) {
+            const int p = order[host_rowptr[xj] + i];
+            ell[((size_t)i * h->M + xj) * 2] = sp_label_slot(host_cols[p]);
+            ell[((size_t)i * h->M + xj) * 2 + 1] = wbits[p];
+        }
+    void *bufs[] = {h->d_sp_len, h->d_sp_ell};
     for (void *p : bufs)
         if (p) cudaFree(p);
-    h->d_sp_rowptr = h->d_sp_cols = h->d_sp_w = nullptr;
-    const size_t cb = (size_t)(nnz > 0 ? nnz : 1) * 4;
-    if (bp_status st = ensure_buffer(h, &h->d_sp_rowptr, (size_t)(h->M + 1) * 4, "sparse rowptr")) return st;
-    if (bp_status st = ensure_buffer(h, &h->d_sp_cols, cb, "sparse columns")) return st;
-    if (bp_status st = ensure_buffer(h, &h->d_sp_w, cb, "sparse values")) return st;
-    BP_CK(h, cudaMemcpyAsync(h->d_sp_rowptr, h->sp_rowptr.data(), (size_t)(h->M + 1) * 4, cudaMemcpyHostToDevice,
-                             h->stream));
-    if (nnz > 0) {
-        BP_CK(h, cudaMemcpyAsync(h->d_sp_cols, h->sp_cols.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, h->stream));
-        BP_CK(h, cudaMemcpyAsync(h->d_sp_w, h->dtype == BP_F32 ? (const void *)wf.data() : (const void *)wi.data(),
-                                 (size_t)nnz * 4, cudaMemcpyHostToDevice, h->stream));
-    }
+    h->d_sp_len = h->d_sp_ell = nullptr;
+    if (bp_status st = ensure_buffer(h, &h->d_sp_len, (size_t)h->M * 4, "sparse row lengths")) return st;
+    if (bp_status st = ensure_buffer(h, &h->d_sp_ell, ell.size() * 4, "sparse pattern")) return st;
+    BP_CK(h, cudaMemcpyAsync(h->d_sp_len, len.data(), (size_t)h->M * 4, cudaMemcpyHostToDevice, h->stream));
+    BP_CK(h, cudaMemcpyAsync(h->d_sp_ell, ell.data(), ell.size() * 4, cudaMemcpyHostToDevice, h->stream));
     BP_CK(h, cudaStreamSynchronize(h->stream));
     if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
     h->sparse = true;

@@ -58,7 +58,7 @@ struct bp_ctx {
     std::vector<int32_t> sp_rowptr, sp_cols;
     std::vector<float> sp_valf;      // f(x_i, x_j)
     std::vector<int32_t> sp_vali;    // E(x_i, x_j)
-    void *d_sp_rowptr = nullptr, *d_sp_cols = nullptr, *d_sp_w = nullptr;
+    void *d_sp_len = nullptr, *d_sp_ell = nullptr;   // device pattern (see bp_sparse.h)
 
     bpg::Layout layout{32, 1};
     bpg::Layout log_layout{32, 1};  // layout of the log-domain forward and adjoint kernels

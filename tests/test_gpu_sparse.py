@@ -117,3 +117,45 @@ def test_sparse_max_mode_rejects_energy_above_ebar():
         bp.bp_set_potential_sparse(G.h, rowptr, np.array([8], np.int32), np.array([1], np.int32), 5, bp.BP_I32)
     assert ei.value.status == bp.BP_ERR_ARG
     G.close()
+
+
+@pytest.mark.parametrize("dtype_name", ["f32", "i32"])
+def test_sparse_long_rows_at_the_largest_label_count(dtype_name):
+    """M = 300 (padded to 512 labels: 16 receiver labels per lane), rows from
+    empty up to every label (the dense row), against the dense oracle."""
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(300)
+    M, W, Hh = 300, 5, 4
+    lens = rng.integers(0, 40, M)
+    lens[[0, 7, M - 1]] = [M, 0, M]
+    rowptr, cols = [0], []
+    for xj in range(M):
+        cols.extend(int(x) for x in rng.choice(M, size=int(lens[xj]), replace=False))
+        rowptr.append(len(cols))
+    rowptr, cols = np.array(rowptr, np.int32), np.array(cols, np.int32)
+    if dtype_name == "f32":
+        vals = rng.uniform(0.05, 2.0, len(cols)).astype(np.float32)
+        g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
+        bel, mp, pl = _run(M, bp.BP_F32, None, g, (rowptr, cols, vals), 0.1, 2, "sync")
+        F = stereo.sparse_compatibility_matrix(rowptr, cols, vals.astype(np.float64), 0.1, M)
+        p64, b64 = grid.grid_sum_product(g.astype(np.float64), F, 2, "sync")
+        assert H.node_rel_err(bel, b64) <= H.REL_TOL
+        assert H.message_rel_err(pl, p64, W, Hh) <= H.REL_TOL
+    else:
+        ebar = 25
+        vals = rng.integers(0, ebar + 1, len(cols)).astype(np.int32)
+        E = rng.integers(0, 30, (Hh, W, M)).astype(np.int32)
+        bel, mp, pl = _run(M, bp.BP_I32, None, E, (rowptr, cols, vals), ebar, 2, "sync")
+        V = stereo.sparse_compatibility_matrix(rowptr, cols, vals.astype(np.int64), ebar, M, dtype=np.int64)
+        p64, b64 = grid.grid_min_sum(E.astype(np.int64), V, 2, "sync")
+        np.testing.assert_array_equal(bel.astype(np.int64), b64)
+
+
+def test_sparse_rejects_more_than_512_labels():
+    from paper_1010_0012_gb300 import bp
+    G = bp.BPGrid(3, 3, 600, bp.BP_F32)
+    rowptr = np.zeros(601, np.int32)
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_set_potential_sparse(G.h, rowptr, np.zeros(0, np.int32), np.zeros(0, np.float32), 0.5, bp.BP_F32)
+    assert ei.value.status == bp.BP_ERR_UNSUPPORTED
+    G.close()
