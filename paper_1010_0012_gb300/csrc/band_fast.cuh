@@ -336,20 +336,107 @@ __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
 template <int L, int C, int T, bool COH>
 struct MinBand {
     static constexpr int V = 4 * C;
+    static constexpr int VP = V / 2;            // label pairs per lane (packed form)
+    static constexpr int TP = (T + 1) / 2;      // halo pairs on each side
     int32_t w[2 * T + 1];
     int32_t ebar;
     bool lab_ok[V];
     bool zero_min;
     int q;
+    // packed form: E'(d) = E(d) - Emin in both halves, Ebar' = Ebar - Emin
+    bool p16;
+    uint32_t wp[2 * T + 1];
+    uint32_t keep[VP];                          // 0xffff per half that holds a label < M
+    int32_t ebar16;
 
-    __device__ __forceinline__ void setup(const int32_t *wsrc, int32_t eb, int M, int lane_q, bool zmin = false) {
+    __device__ __forceinline__ void setup(const int32_t *wsrc, int32_t eb, int M, int lane_q, bool zmin = false,
+                                          bool packed = false) {
         q = lane_q;
         ebar = eb;
         zero_min = zmin;
+        int32_t emin = eb;
 #pragma unroll
-        for (int i = 0; i < 2 * T + 1; ++i) w[i] = wsrc[i];
+        for (int i = 0; i < 2 * T + 1; ++i) {
+            w[i] = wsrc[i];
+            emin = min(emin, w[i]);
+        }
 #pragma unroll
         for (int k = 0; k < V; ++k) lab_ok[k] = q * V + k < M;
+        p16 = packed;
+        ebar16 = eb - emin;
+#pragma unroll
+        for (int i = 0; i < 2 * T + 1; ++i) wp[i] = (uint32_t)(w[i] - emin) * 0x10001u;
+#pragma unroll
+        for (int k = 0; k < VP; ++k) keep[k] = (lab_ok[2 * k] ? 0xffffu : 0u) | (lab_ok[2 * k + 1] ? 0xffff0000u : 0u);
+    }
+
+    // Eq. 11 on 16-bit label pairs, exact when Ebar - Emin <= 16000 (the host
+    // decides).  With h' = min(h - Hmin, Ebar' + 1) and E' = E - Emin,
+    //   u'(x) = min(Ebar', min_d E'(d) + h'(x + d))
+    // equals u(x) - Hmin - Emin: a clamped term is > Ebar' >= u'(x) either way,
+    // so the clamp never changes the minimum, and every value stays below
+    // 2 Ebar' + 2 <= 32002.  Two labels per DPX add-min instead of one.
+    __device__ __forceinline__ void band_packed(const int32_t (&h)[V], int32_t hmin, int32_t (&u)[V]) const {
+        const int32_t cap = hmin + ebar16 + 1;
+        uint32_t hp[VP];
+#pragma unroll
+        for (int k = 0; k < VP; ++k) {
+            const uint32_t lo = (uint32_t)(min(h[2 * k], cap) - hmin);
+            const uint32_t hi = (uint32_t)(min(h[2 * k + 1], cap) - hmin);
+            hp[k] = lo | (hi << 16);
+        }
+        const uint32_t none = (uint32_t)(ebar16 + 1) * 0x10001u;
+        uint32_t win[VP + 2 * TP];                 // pairs of labels qV - 2TP + 2j, + 1
+        band_window<L, VP, TP, uint32_t>(win, hp, q, none);
+        uint32_t odd[VP + 2 * TP - 1];             // pairs starting one label later
+#pragma unroll
+        for (int j = 0; j + 1 < VP + 2 * TP; ++j) odd[j] = __byte_perm(win[j], win[j + 1], 0x5432);
+        const uint32_t flat = (uint32_t)ebar16 * 0x10001u;
+        uint32_t acc[VP];
+#pragma unroll
+        for (int k = 0; k < VP; ++k) {
+            uint32_t a = flat;
+#pragma unroll
+            for (int d = -T; d <= T; ++d) {
+                const int r = 2 * k + d + 2 * TP;  // window position of label pair (2k + d, 2k + d + 1)
+                const uint32_t term = (r & 1) ? odd[(r - 1) / 2] : win[r / 2];
+                a = __viaddmin_s16x2(wp[d + T], term, a);
+            }
+            acc[k] = (a & keep[k]) | (flat & ~keep[k]);   // labels >= M: Ebar', never below the minimum
+        }
+        int32_t umin;
+        if (zero_min) {
+            umin = (int32_t)(wp[T] & 0xffffu);
+        } else {
+            uint32_t m2 = acc[0];
+#pragma unroll
+            for (int k = 1; k < VP; ++k) m2 = __vimin_s16x2_relu(m2, acc[k]);   // halves are >= 0
+            umin = group_min<L>(min((int32_t)(m2 & 0xffffu), (int32_t)(m2 >> 16)));
+        }
+        const uint32_t sub = (uint32_t)umin * 0x10001u;
+#pragma unroll
+        for (int k = 0; k < VP; ++k) {
+            const uint32_t o = (acc[k] - sub) & keep[k];    // no borrow: every half >= umin
+            u[2 * k] = (int32_t)(o & 0xffffu);
+            u[2 * k + 1] = (int32_t)(o >> 16);
+        }
+    }
+
+    // Eq. 11 on int32 labels: one DPX add-min per band term
+    __device__ __forceinline__ void band_int(const int32_t (&h)[V], int32_t hmin, int32_t (&u)[V]) const {
+        int32_t win[V + 2 * T];
+        band_window<L, V, T, int32_t>(win, h, q, kIntBig);
+        const int32_t flat = ebar + hmin;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            int32_t b = flat;
+#pragma unroll
+            for (int d = -T; d <= T; ++d) b = __viaddmin_s32(w[d + T], win[T + k + d], b);
+            u[k] = lab_ok[k] ? b : kIntBig;
+        }
+        const int32_t umin = zero_min ? w[T] + hmin : group_min<L>(min_vec<V>(u));
+#pragma unroll
+        for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
     }
 
     __device__ __forceinline__ void node(const int32_t *e, const int32_t *in, int32_t *out, int W, int H, int Mp,
@@ -364,36 +451,29 @@ struct MinBand {
             if (has[s]) ld_msg<COH, V>(m[s], in + s * plane + off);
             else fill_vec<V, int32_t>(m[s], 0);
         }
+        // E_u + all four messages once per label (labels >= M: kIntBig); the
+        // h of direction t is that total minus the message from side t
+        int32_t tot[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) tot[k] = lab_ok[k] ? ev[k] + m[0][k] + m[1][k] + m[2][k] + m[3][k] : kIntBig;
 
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             int32_t h[V];
 #pragma unroll
-            for (int k = 0; k < V; ++k) {
-                int32_t s = ev[k];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (u != t) s += m[u][k];
-                h[k] = lab_ok[k] ? s : kIntBig;
-            }
+            for (int k = 0; k < V; ++k) h[k] = tot[k] - m[t][k];
             int32_t hmin = min_vec<V>(h);
             hmin = group_min<L>(hmin);
 
-            int32_t win[V + 2 * T];
-            band_window<L, V, T, int32_t>(win, h, q, kIntBig);
-            const int32_t flat = ebar + hmin;
             int32_t u[V];
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                // min(E(d) + h(x + d), running min) in one DPX add-min per band term
-                int32_t b = flat;
-#pragma unroll
-                for (int d = -T; d <= T; ++d) b = __viaddmin_s32(w[d + T], win[T + k + d], b);
-                u[k] = lab_ok[k] ? b : kIntBig;
+            // the packed form pays from T = 3 on; narrower bands keep the
+            // int32 form only (and its register count)
+            if constexpr (T >= 3) {
+                if (p16) band_packed(h, hmin, u);
+                else band_int(h, hmin, u);
+            } else {
+                band_int(h, hmin, u);
             }
-            const int32_t umin = zero_min ? w[T] + hmin : group_min<L>(min_vec<V>(u));
-#pragma unroll
-            for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, u);
         }
     }
@@ -404,7 +484,7 @@ __global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
     constexpr int GPB = kBlock / L;
     const int grp = threadIdx.x / L;
     MinBand<L, C, T, false> band;
-    band.setup(a.w, a.ebar, a.d.M, threadIdx.x & (L - 1), a.zero_min != 0);
+    band.setup(a.w, a.ebar, a.d.M, threadIdx.x & (L - 1), a.zero_min != 0, a.packed16 != 0);
     const int W = a.d.W;
     const int nslots = num_slots(W, a.d.H, a.parity);
     for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {

@@ -90,7 +90,7 @@ __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int n
     void *out = parity < 0 ? m->msg[src ^ 1] : m->msg[src];
     if (MIN) {
         MinBand<L, C, T, true> b;
-        b.setup(m->wi, m->ebar, m->M, q, m->zero_min != 0);
+        b.setup(m->wi, m->ebar, m->M, q, m->zero_min != 0, m->packed16 != 0);
         for (int base = 0; base < count; base += GPB) {
             int r = 0, c = 0;
             bool valid = base + grp < count;

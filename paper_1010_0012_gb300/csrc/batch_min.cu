@@ -1,12 +1,16 @@
-// Instantiations of the persistent batch kernel, min-sum int32.
-#include "batch_kernels.cuh"
+// Launch of the persistent batch kernel, min-sum int32.
 #include "band_dispatch.cuh"
+#include "bp_batch_internal.h"
 
 namespace bpg {
 
+const void *batch_min_kernel_f1();   // batch_min_f1.cu
+const void *batch_min_kernel_f2();   // batch_min_f2.cu
+const void *batch_min_kernel_rb();   // batch_min_rb.cu
+
 static const void *batch_min_fn(int family, bool redblack = false) {
-    if (redblack) return (const void *)batch_kernel<1, true, true>;
-    return family == 2 ? (const void *)batch_kernel<2, true, false> : (const void *)batch_kernel<1, true, false>;
+    if (redblack) return batch_min_kernel_rb();
+    return family == 2 ? batch_min_kernel_f2() : batch_min_kernel_f1();
 }
 
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s) {

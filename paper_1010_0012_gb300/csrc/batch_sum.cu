@@ -1,12 +1,16 @@
-// Instantiations of the persistent batch kernel, sum-product FP32.
-#include "batch_kernels.cuh"
+// Launch of the persistent batch kernel, sum-product FP32.
 #include "band_dispatch.cuh"
+#include "bp_batch_internal.h"
 
 namespace bpg {
 
+const void *batch_sum_kernel_f1();   // batch_sum_f1.cu
+const void *batch_sum_kernel_f2();   // batch_sum_f2.cu
+const void *batch_sum_kernel_rb();   // batch_sum_rb.cu
+
 static const void *batch_sum_fn(int family, bool redblack = false) {
-    if (redblack) return (const void *)batch_kernel<1, false, true>;
-    return family == 2 ? (const void *)batch_kernel<2, false, false> : (const void *)batch_kernel<1, false, false>;
+    if (redblack) return batch_sum_kernel_rb();
+    return family == 2 ? batch_sum_kernel_f2() : batch_sum_kernel_f1();
 }
 
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s) {

@@ -148,6 +148,7 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
                 for (int i = 0; i < 2 * h->Teff + 1; ++i) a.w[i] = h->wi[i];
                 a.ebar = h->ebar;
                 a.zero_min = bpg_zero_min(h->wi) ? 1 : 0;
+                a.packed16 = bpg_packed16(h->wi, h->ebar) ? 1 : 0;
                 e = launch_band_min(a, h->layout, h->blocks_override, h->stream);
             } else {
                 BandArgsGenericI a{(const int32_t *)h->unary, (const int32_t *)in, (int32_t *)out, h->dims,
@@ -206,6 +207,7 @@ static bp_status persistent_setup(bp_ctx *h) {
         for (int i = 0; i < 2 * h->Teff + 1; ++i) m.wi[i] = h->wi[i];
         m.ebar = h->ebar;
         m.zero_min = bpg_zero_min(h->wi) ? 1 : 0;
+        m.packed16 = bpg_packed16(h->wi, h->ebar) ? 1 : 0;
     }
     if (bp_status st = ensure_buffer(h, &h->p_mrf, sizeof(BatchMrf), "persistent descriptor")) return st;
     if (bp_status st = ensure_buffer(h, &h->p_bar, kBatchCtlWords * sizeof(unsigned), "barrier words")) return st;
@@ -337,6 +339,12 @@ bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_h
     Layout lays[8];
     const int nlay = std::min(8, layouts_for(Mp, lays, 8));
     h->layout = nlay > 0 ? lays[0] : Layout{32, 1};
+    // two chunks per lane halve the threads per node: on grids that then fill
+    // the GPU fewer than four times over (384x288, M = 16: one red-black
+    // half-step is 55k nodes) one chunk per lane keeps the SMs occupied
+    if (h->layout.C == 2 && (long long)W * H * (Mp / 8) < 4LL * device_sm_count() * 2048)
+        for (int i = 0; i < nlay; ++i)
+            if (lays[i].C == 1) { h->layout = lays[i]; break; }
     // the log-domain kernels (an exp per h entry, a log per output, and the
     // adjoint's extra state per label) keep one chunk per lane: the same
     // rounding path for the recorded forward and its adjoint
@@ -881,6 +889,15 @@ bp_status bp_set_checkpoint_interval(bp_handle h, int every) {
 }
 
 }  // extern "C"
+
+// True when the min-sum band of this table runs exactly on 16-bit label pairs
+// (MinBand::band_packed): Ebar - min_d E(d) <= 16000.
+bool bpg_packed16(const std::vector<int32_t> &w, int32_t ebar) {
+    if (w.empty()) return false;
+    int64_t emin = ebar;
+    for (int32_t v : w) emin = std::min<int64_t>(emin, v);
+    return (int64_t)ebar - emin <= 16000;
+}
 
 // True when the centre entry E(0) of a band table (2T+1 entries) is its minimum.
 bool bpg_zero_min(const std::vector<int32_t> &w) {

@@ -283,6 +283,7 @@ bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void 
                 wv.push_back(t[dd + d.T]);
             }
             x.zero_min = bpg_zero_min(wv) ? 1 : 0;
+            x.packed16 = bpg_packed16(wv, x.ebar) ? 1 : 0;
         }
     }
     if (st == BP_OK) {

@@ -20,6 +20,7 @@ struct BatchMrf {
     int32_t wi[2 * kTMaxFast + 1];  // E(d) (min-sum)
     int32_t ebar;
     int zero_min;                   // 1 if E(0) is the table's minimum
+    int packed16;                   // 1: min-sum band on 16-bit label pairs (see MinBand)
 };
 
 // A run of `count` consecutive slots of one MRF: nodes for a synchronous

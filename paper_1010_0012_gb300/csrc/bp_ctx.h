@@ -118,6 +118,7 @@ cudaError_t bpg_issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int &c
 bp_status bpg_record_forward(bp_ctx *h, int n_iters);   // bp_backward.cu
 float bpg_pair_value_f(const bp_ctx *h, int xi, int xj);   // bp_api.cu
 bool bpg_zero_min(const std::vector<int32_t> &w);
+bool bpg_packed16(const std::vector<int32_t> &w, int32_t ebar);
 int32_t bpg_pair_value_i(const bp_ctx *h, int xi, int xj);
 void bpg_free_extras(bp_ctx *h);                         // bp_backward.cu
 bp_status bpg_dense_tc_iterate(bp_ctx *h, int n_iters);  // dense_tc.cu

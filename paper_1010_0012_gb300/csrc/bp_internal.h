@@ -43,6 +43,7 @@ struct BandArgsI {
     int32_t w[2 * kTMaxFast + 1];  // E(d), d = -T..T
     int32_t ebar;
     int zero_min;                  // 1 if E(0) is the table's minimum
+    int packed16;                  // 1: Ebar - min E(d) <= 16000, the band runs on 16-bit label pairs
 };
 
 // Shared-memory O(mM) kernels for any T (table on the device).
