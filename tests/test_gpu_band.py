@@ -229,3 +229,20 @@ def test_persistent_issue_is_one_launch_per_call():
     assert G.launches - n1 == 100
     G.sync()
     G.close()
+
+
+@pytest.mark.parametrize("ebar", [16000, 16001, 90000])
+@pytest.mark.parametrize("T", [3, 8])
+def test_min_sum_16_bit_pairs_boundary_and_large_energies(ebar, T):
+    """The 16-bit pair form of the min-sum band serves Ebar - min E(d) <= 16000
+    (16000: pairs; 16001 and 90000: int32).  Large unaries and incoming
+    messages make h exceed the clamp; every message must still equal the
+    oracle's exactly."""
+    rng = np.random.default_rng(ebar + T)
+    M, W, Hh = 64, 9, 7
+    tab = rng.integers(0, ebar + 1, 2 * T + 1).astype(np.int32)
+    tab[T] = 0
+    E = rng.integers(0, 60000, (Hh, W, M)).astype(np.int32)
+    planes = H.random_planes_min(W, Hh, M, rng, hi=ebar)
+    H.check_min_case(E, tab, T, ebar, 3, "sync", planes0=planes)
+    H.check_min_case(E, tab, T, ebar, 2, "redblack", planes0=planes)
