@@ -130,7 +130,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, pw = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -141,12 +141,17 @@ class ClockSampler:
                 mx = float(f[2])
             except ValueError:
                 continue
+            try:
+                pw.append(float(f[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "power_w": statistics.median(pw) if pw else None}
 
 
 # --------------------------------------------------------------- CPU oracle ----
@@ -293,6 +298,7 @@ def run_ours(args, cfg, rank, world):
         ready = [torch.cuda.Event() for _ in range(2)]
         consumed = [None, None]
         torch.cuda.synchronize()
+        clk_e = ClockSampler(dev).__enter__()
         e0 = time.perf_counter()
 
         def upload(i):
@@ -317,8 +323,11 @@ def run_ours(args, cfg, rank, world):
         stream.synchronize()
         G.sync()
         torch.cuda.synchronize()
-        out["e2e"] = {"value": units_step * n_e * world / (time.perf_counter() - e0), "unit": UNIT,
-                      "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(map_host[0].numel() * 4)}
+        e_wall = time.perf_counter() - e0
+        clk_e.__exit__()
+        out["e2e"] = {"value": units_step * n_e * world / e_wall, "unit": UNIT,
+                      "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(map_host[0].numel() * 4),
+                      "steps": n_e, "clocks": clk_e.summary()}
 
     # O(M^2) baselines on the same grid and state, timed per iteration
     if not args.no_baselines:
