@@ -432,6 +432,66 @@ def run_batch_workload(args):
     print(json.dumps(line))
 
 
+def run_dense_compare_workload(args):
+    """The O(mM) update against the O(M^2) baselines on the same 1280x720
+    grid at M = 64 (T = 3) and M = 128 (T = 4): time per synchronous
+    sum-product iteration of each (CUDA events, median of 5 runs of 5
+    iterations after a warm-up run)."""
+    import dataclasses
+    import torch
+    from paper_1010_0012_gb300 import bp
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    pk = peaks()
+    out = {}
+    for M, T in ((64, 3), (128, 4)):
+        cfg = dataclasses.replace(wl.CONFIGS["grid1280x720_m128"], M=M, T=T)
+        st = wl.make_stereo(cfg)
+        u = torch.from_numpy(wl.unary_f32(st)).cuda()
+        torch.cuda.synchronize()
+        G = bp.BPGrid(cfg.W, cfg.H, M, bp.BP_F32, stream=stream)
+        G.set_unary(u)
+        tab, fbar = wl.pair_table_f32(cfg.alpha, T)
+        G.set_potential(tab, T, fbar)
+        n_it = 5
+        runs = {"band_mM": lambda: G.iterate(n_it, bp.BP_SUM, "sync")}
+        for name, kind in (("dense_bf16_tcgen05_fused", bp.BP_DENSE_BF16_TC_FUSED),
+                           ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC),
+                           ("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE)):
+            runs[name] = (lambda k: (lambda: bp.bp_iterate_dense(G.h, n_it, k)))(kind)
+        res = {}
+        for name, fn in runs.items():
+            G.reset()
+            G.iterate(0, bp.BP_SUM, "sync")
+            fn()
+            G.sync()
+            ts = []
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b) / 1e3 / n_it)
+            t = statistics.median(ts)
+            ach = algorithmic_bytes(cfg) / t / 1e9
+            res[name] = {"value": workload_units(cfg) / t, "unit": UNIT, "ms_per_iter": t * 1e3,
+                         "hbm_frac_at_9_bytes_per_update": ach / pk["hbm_gbs"]}
+        G.sync()
+        res["band_over_fused_tcgen05"] = res["band_mM"]["value"] / res["dense_bf16_tcgen05_fused"]["value"]
+        res["layout"] = list(bp.bp_get_layout(G.h))
+        out[f"M{M}_T{T}"] = res
+        G.close()
+        del u
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC + " vs the O(M^2) baselines", "value": out["M64_T3"]["band_mM"]["value"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "1280x720 random-dot stereo, synchronous sum-product, M = 64 (T = 3) and "
+                                   "M = 128 (T = 4); the O(M^2) updates run on the same grid and state"},
+            "peak_source": pk["source"], "modes": out}
+    print(json.dumps(line))
+
+
 def run_grid_workload(args, name):
     """A single grid in both modes on its own schedule (e.g. 384x288 red-black)."""
     import torch
@@ -670,6 +730,9 @@ def run_factor_workload(args):
 
 def main():
     args = parse_args()
+    if args.impl == "ours" and args.workload == "dense_compare":
+        run_dense_compare_workload(args)
+        return 0
     if args.impl == "ours" and args.workload == "factor256":
         run_factor_workload(args)
         return 0
