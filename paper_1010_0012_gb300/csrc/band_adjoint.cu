@@ -26,8 +26,17 @@
 
 namespace bpg {
 
-template <int L, int C, int T>
-__global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs a) {
+// One chunk per lane and T <= 4 (kEarly): the kernel is held to 80 registers
+// so that three blocks (24 warps) share an SM, and every load of a node is
+// issued at once; the extra warps hide the latency (72 -> 61 us at 256x256,
+// M = 64, T = 3, for a few bytes of spill).  Wider layouts and bands would
+// spill heavily: they keep the compiler's register choice and load each
+// direction's adjoint where it is used.
+template <int C, int T>
+__host__ __device__ constexpr bool adjoint_early() { return C == 1 && T <= 4; }
+
+template <int L, int C, int T, bool kEarly>
+__device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
     constexpr int V = 4 * C;
     constexpr int GPB = kBlock / L;
     constexpr int NP = 2 * T + 2;      // dw(-T..T), dfbar
@@ -64,12 +73,24 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
         const long long off = ((long long)r * W + c) * Mp + q * V;
         const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
 
-        float gam[V], l[4][V];
+        // with the 80-register bound (kEarly) every load of the node goes
+        // first: the state, the adjoints of the four outgoing messages and
+        // dL/d log g, one round trip instead of six
+        constexpr int VE = kEarly ? V : 1;
+        float gam[V], l[4][V], lam[4][VE], dgo[VE];
         if (valid) ld_vec<V>(gam, a.logg + off); else fill_vec<V>(gam, 0.f);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             if (has[s]) ld_vec<V>(l[s], a.ell + s * plane + off);
             else fill_vec<V>(l[s], 0.f);
+        }
+        if constexpr (kEarly) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (has[t]) ld_vec<V>(lam[t], a.lam_next + out_offset(t, r, c, W, plane, Mp) + q * V);
+                else fill_vec<V>(lam[t], 0.f);
+            }
+            if (valid) ld_vec<V>(dgo, a.dlogg + off); else fill_vec<V>(dgo, 0.f);
         }
         float dl[4][V], dg[V];
 #pragma unroll
@@ -108,8 +129,13 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
 
             // adjoint of the stored message
             float del[V];
-            if (has[t]) ld_vec<V>(del, a.lam_next + out_offset(t, r, c, W, plane, Mp) + q * V);
-            else fill_vec<V>(del, 0.f);
+            if constexpr (kEarly) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) del[k] = lam[t][k % VE];
+            } else {
+                if (has[t]) ld_vec<V>(del, a.lam_next + out_offset(t, r, c, W, plane, Mp) + q * V);
+                else fill_vec<V>(del, 0.f);
+            }
             float nd = 0.f;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
@@ -161,7 +187,13 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
 #pragma unroll
         for (int s = 0; s < 4; ++s)
             if (has[s]) st_vec<V>(a.lam + s * plane + off, dl[s]);
-        if (valid) {
+        if constexpr (kEarly) {
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < V; ++k) dg[k] += dgo[k % VE];
+                st_vec<V>(a.dlogg + off, dg);
+            }
+        } else if (valid) {
             float acc[V];
             ld_vec<V>(acc, a.dlogg + off);
 #pragma unroll
@@ -188,9 +220,22 @@ __global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs 
     }
 }
 
+template <int L, int C, int T>
+__global__ void __launch_bounds__(kBlock) band_log_adjoint_kernel(const AdjArgs a) {
+    adjoint_body<L, C, T, false>(a);
+}
+
+template <int L, int C, int T>
+__global__ void __launch_bounds__(kBlock, 3) band_log_adjoint_kernel_3pm(const AdjArgs a) {
+    adjoint_body<L, C, T, true>(a);
+}
+
 struct AdjTag {
     template <int L, int C, int T>
-    static const void *get() { return (const void *)band_log_adjoint_kernel<L, C, T>; }
+    static const void *get() {
+        if constexpr (adjoint_early<C, T>()) return (const void *)band_log_adjoint_kernel_3pm<L, C, T>;
+        else return (const void *)band_log_adjoint_kernel<L, C, T>;
+    }
 };
 
 int adjoint_blocks(const GridDims &d, Layout lay, int T) {
