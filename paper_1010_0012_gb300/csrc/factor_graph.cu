@@ -79,22 +79,38 @@ __global__ void v2f_kernel(const E *unary, const int32_t *var_ptr, const int32_t
 }
 
 // ---- factor -> variable: the O(C + M) update -----------------------------------
-// Block shared memory holds, per slot s, the triplets ordered by x_s (CSR
-// ptr_s[M+1]) as (other labels packed x_u | x_w << 16, weight bits); each warp
-// stages its factor's three incoming vectors.
-template <bool MIN, typename E>
-__global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, const int32_t *ptr, const int2 *ent,
-                                                       int C, FgDims d, E fbar_or_ebar) {
+// The triplet list is held per slot s and output label x_s as a list of
+// (x_u | x_w << 16, weight bits), interleaved by label (entry i of label x at
+// base_s + i * M + x: consecutive lanes read consecutive words, through L1,
+// where the table stays) and sorted by the offsets (x_u - x_s, x_w - x_s) mod M,
+// so that at each step the lanes gather n_u and n_w from different banks of
+// the warp's shared-memory copy of the incoming messages.  One warp per factor;
+// lane l produces labels l, l + 32, ... (KM of them) and walks their lists side
+// by side.
+struct FgTable {
+    const int2 *ell;        // [sum_s rows_s * M]
+    const int32_t *len;     // [3][M]
+    long long base[3];      // start of slot s in ell
+};
+
+template <bool MIN, typename E, int KM>
+__global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, const FgTable tab, FgDims d,
+                                                       E fbar_or_ebar) {
     extern __shared__ uint8_t sm[];
     const int M = d.M, Mp = d.Mp;
-    int *sptr = (int *)sm;                                        // [3][M + 1]
-    int2 *sent = (int2 *)(sm + ((3 * (M + 1) * 4 + 15) & ~15));   // [3][C]
-    E *sn = (E *)((uint8_t *)sent + (size_t)3 * C * 8);           // [warps][3][Mp]
-    for (int i = threadIdx.x; i < 3 * (M + 1); i += kFgBlock) sptr[i] = ptr[i];
-    for (int i = threadIdx.x; i < 3 * C; i += kFgBlock) sent[i] = ent[i];
-    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    E *n = sn + warp * 3 * Mp;
+    E *n = (E *)sm + warp * 3 * Mp;                       // [3][Mp] per warp
+    int len[3][KM], len_max[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        len_max[s] = 0;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int x = lane + 32 * k;
+            len[s][k] = x < M ? tab.len[s * M + x] : 0;
+            len_max[s] = max(len_max[s], len[s][k]);
+        }
+    }
     const long long gw = (long long)blockIdx.x * kFgWarps + warp, nw = (long long)gridDim.x * kFgWarps;
     for (long long a = gw; a < d.n_factors; a += nw) {
         E red[3];
@@ -114,49 +130,50 @@ __global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, c
                 if (MIN) red[s] = y < red[s] ? y : red[s]; else red[s] += y;
             }
         __syncwarp();
+#pragma unroll
         for (int s = 0; s < 3; ++s) {
             const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;   // the other two slots, in order
+            const E *nu = n + u * Mp, *nwv = n + w * Mp;
             const E flat = MIN ? fbar_or_ebar + red[u] + red[w] : fbar_or_ebar * red[u] * red[w];
-            E norm = MIN ? E(kBig) : E(0);
-            E outv[8];   // M <= 256: at most 8 labels per lane
+            const int2 *ell = tab.ell + tab.base[s];
+            E acc[KM];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int x = lane + 32 * k;
-                if (k * 32 >= Mp) break;
-                E acc = MIN ? flat : E(0);
-                if (x < M) {
-                    for (int p = sptr[s * (M + 1) + x]; p < sptr[s * (M + 1) + x + 1]; ++p) {
-                        const int2 e = sent[(size_t)s * C + p];
-                        const int xu = e.x & 0xffff, xw = e.x >> 16;
-                        if (MIN) {
-                            const E t = e.y + n[u * Mp + xu] + n[w * Mp + xw];
-                            acc = t < acc ? t : acc;
-                        } else {
-                            acc = fmaf(__int_as_float(e.y), n[u * Mp + xu] * n[w * Mp + xw], acc);
-                        }
+            for (int k = 0; k < KM; ++k) acc[k] = MIN ? flat : E(0);
+            for (int i = 0; i < len_max[s]; ++i) {
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (i < len[s][k]) {
+                        const int2 e = __ldg(ell + (long long)i * M + lane + 32 * k);
+                        const E gu = nu[e.x & 0xffff], gwv = nwv[e.x >> 16];
+                        if (MIN) acc[k] = __viaddmin_s32(e.y, gu + gwv, acc[k]);
+                        else acc[k] = fmaf(__int_as_float(e.y), gu * gwv, acc[k]);
                     }
-                    if (!MIN) acc += flat;
-                    if (MIN) norm = acc < norm ? acc : norm; else norm += acc;
                 }
-                outv[k] = acc;
+            }
+            E norm = MIN ? E(kBig) : E(0);
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                if (lane + 32 * k < M) {
+                    if (!MIN) acc[k] += flat;
+                    if (MIN) norm = acc[k] < norm ? acc[k] : norm; else norm += acc[k];
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const E y = __shfl_xor_sync(0xffffffffu, norm, o);
                 if (MIN) norm = y < norm ? y : norm; else norm += y;
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < KM; ++k) {
                 const int x = lane + 32 * k;
-                if (k * 32 >= Mp) break;
                 if (x < Mp) {
                     E v;
-                    if (MIN) v = x < M ? outv[k] - norm : E(0);
-                    else v = x < M ? outv[k] / norm : E(0);
+                    if (MIN) v = x < M ? acc[k] - norm : E(0);
+                    else v = x < M ? acc[k] / norm : E(0);
                     m_fv[(a * 3 + s) * Mp + x] = v;
                 }
             }
         }
-        __syncwarp();
+        __syncwarp();   // the warp's copy of the messages is rewritten for its next factor
     }
 }
 
@@ -283,8 +300,9 @@ struct bp_fg_ctx {
     void *unary = nullptr;
     int32_t *var_ptr = nullptr, *var_inc = nullptr;
     void *m_fv = nullptr, *n_vf = nullptr;
-    int32_t *d_ptr = nullptr;
-    int2 *d_ent = nullptr;
+    int32_t *d_len = nullptr;   // [3][M] list lengths
+    int2 *d_ell = nullptr;      // interleaved triplet lists (FgTable)
+    long long ell_base[3] = {0, 0, 0};
     void *d_dense = nullptr;
     int C = 0;
     double fbar = 0;
@@ -309,15 +327,26 @@ static bp_status fgfail(bp_factor_graph g, bp_status st, const std::string &m) {
                           std::string(#call) + ": " + cudaGetErrorString(e_));                         \
     } while (0)
 
-static size_t f2v_smem(int M, int Mp, int C, int elem) {
-    return (size_t)((3 * (M + 1) * 4 + 15) & ~15) + (size_t)3 * C * 8 + (size_t)kFgWarps * 3 * Mp * elem;
-}
+static size_t f2v_smem(int Mp, int elem) { return (size_t)kFgWarps * 3 * Mp * elem; }
 
 static int warp_grid(long long items) {
     long long b = (items * 32 + 255) / 256;
     const long long cap = (long long)bpg::device_sm_count() * 16;
     if (b > cap) b = cap;
     return (int)(b < 1 ? 1 : b);
+}
+
+template <bool MIN, typename E, int KM>
+static cudaError_t launch_f2v(bp_factor_graph g, const FgTable &tab, const FgDims &d) {
+    const size_t smem = f2v_smem(g->Mp, sizeof(E));
+    const void *fn = (const void *)f2v_kernel<MIN, E, KM>;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFgBlock, smem);
+    long long blocks = (long long)bpg::device_sm_count() * std::max(1, per_sm);
+    blocks = std::min<long long>(blocks, (g->n_factors + kFgWarps - 1) / kFgWarps);
+    f2v_kernel<MIN, E, KM><<<(int)blocks, kFgBlock, smem, g->stream>>>((const E *)g->n_vf, (E *)g->m_fv, tab, d,
+                                                                      (E)g->fbar);
+    return cudaGetLastError();
 }
 
 extern "C" {
@@ -328,7 +357,7 @@ long long bp_fg_launch_count(bp_factor_graph g) { return g ? g->launches : -1; }
 void bp_fg_destroy(bp_factor_graph g) {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
-    void *bufs[] = {g->unary, g->var_ptr, g->var_inc, g->m_fv, g->n_vf, g->d_ptr, g->d_ent, g->d_dense};
+    void *bufs[] = {g->unary, g->var_ptr, g->var_inc, g->m_fv, g->n_vf, g->d_len, g->d_ell, g->d_dense};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
@@ -407,8 +436,6 @@ bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplet
     if (C < 0 || (C > 0 && (!host_triplets || !host_vals)))
         return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: bad triplet list");
     if (!std::isfinite(fbar) || fbar < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: fbar must be >= 0");
-    if (f2v_smem(g->M, g->Mp, C, 4) > 220 * 1024)
-        return fgfail(g, BP_ERR_ARG, "bp_fg_set_factor: too many compatible triplets for shared memory");
     std::vector<char> seen((size_t)g->M * g->M * g->M, 0);
     for (int c = 0; c < C; ++c) {
         const int32_t *t = host_triplets + 3 * c;
@@ -440,28 +467,46 @@ bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplet
         g->vali.assign(v, v + C);
     }
     g->trip.assign(host_triplets, host_triplets + 3 * (size_t)C);
-    // three CSR orders: by x_0, by x_1, by x_2
-    std::vector<int32_t> ptr(3 * (size_t)(g->M + 1), 0);
-    std::vector<int2> ent(3 * (size_t)(C > 0 ? C : 1));
-    for (int s = 0; s < 3; ++s) {
-        int32_t *p = ptr.data() + s * (g->M + 1);
-        for (int c = 0; c < C; ++c) p[host_triplets[3 * c + s] + 1]++;
-        for (int x = 0; x < g->M; ++x) p[x + 1] += p[x];
-        std::vector<int32_t> fillp(p, p + g->M);
-        const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;
-        for (int c = 0; c < C; ++c) {
-            const int32_t *t = host_triplets + 3 * c;
-            ent[(size_t)s * C + fillp[t[s]]++] = make_int2(t[u] | (t[w] << 16), wbits[c]);
+    // per slot s and output label x_s: the list of (x_u, x_w, weight), sorted
+    // by the offsets (x_u - x_s, x_w - x_s) mod M, interleaved by label
+    const int M = g->M;
+    std::vector<std::vector<std::pair<std::pair<int, int>, int2>>> lists((size_t)3 * M);
+    for (int c = 0; c < C; ++c) {
+        const int32_t *t = host_triplets + 3 * c;
+        for (int s = 0; s < 3; ++s) {
+            const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;
+            const int key_u = ((t[u] - t[s]) % M + M) % M, key_w = ((t[w] - t[s]) % M + M) % M;
+            lists[(size_t)s * M + t[s]].push_back({{key_u, key_w}, make_int2(t[u] | (t[w] << 16), wbits[c])});
         }
     }
-    if (g->d_ptr) cudaFree(g->d_ptr);
-    if (g->d_ent) cudaFree(g->d_ent);
+    std::vector<int32_t> len((size_t)3 * M);
+    long long base[3], total = 0;
+    for (int s = 0; s < 3; ++s) {
+        int rows = 0;
+        for (int x = 0; x < M; ++x) {
+            auto &l = lists[(size_t)s * M + x];
+            std::stable_sort(l.begin(), l.end(), [](const auto &p, const auto &q) { return p.first < q.first; });
+            len[(size_t)s * M + x] = (int32_t)l.size();
+            rows = std::max(rows, (int)l.size());
+        }
+        base[s] = total;
+        total += (long long)rows * M;
+    }
+    std::vector<int2> ell((size_t)std::max(1LL, total), make_int2(0, 0));
+    for (int s = 0; s < 3; ++s)
+        for (int x = 0; x < M; ++x) {
+            const auto &l = lists[(size_t)s * M + x];
+            for (size_t i = 0; i < l.size(); ++i) ell[(size_t)(base[s] + (long long)i * M + x)] = l[i].second;
+        }
+    if (g->d_len) cudaFree(g->d_len);
+    if (g->d_ell) cudaFree(g->d_ell);
     if (g->d_dense) cudaFree(g->d_dense);
-    g->d_ptr = nullptr; g->d_ent = nullptr; g->d_dense = nullptr;
-    FG_CK(g, cudaMalloc(&g->d_ptr, ptr.size() * 4));
-    FG_CK(g, cudaMalloc(&g->d_ent, ent.size() * sizeof(int2)));
-    FG_CK(g, cudaMemcpy(g->d_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
-    FG_CK(g, cudaMemcpy(g->d_ent, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    g->d_len = nullptr; g->d_ell = nullptr; g->d_dense = nullptr;
+    FG_CK(g, cudaMalloc(&g->d_len, len.size() * 4));
+    FG_CK(g, cudaMalloc(&g->d_ell, ell.size() * sizeof(int2)));
+    FG_CK(g, cudaMemcpy(g->d_len, len.data(), len.size() * 4, cudaMemcpyHostToDevice));
+    FG_CK(g, cudaMemcpy(g->d_ell, ell.data(), ell.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    for (int s = 0; s < 3; ++s) g->ell_base[s] = base[s];
     g->C = C;
     g->fbar = fbar;
     g->have_factor = true;
@@ -513,22 +558,16 @@ bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode) {
     if (bp_status st = fg_prepare(g, mode)) return st;
     if (g->n_factors == 0) return BP_OK;
     const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
-    const size_t smem = f2v_smem(g->M, g->Mp, g->C, 4);
-    const void *fn = g->dtype == BP_F32 ? (const void *)f2v_kernel<false, float> : (const void *)f2v_kernel<true, int32_t>;
-    FG_CK(g, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFgBlock, smem);
-    long long blocks = (long long)bpg::device_sm_count() * std::max(1, per_sm);
-    blocks = std::min<long long>(blocks, (g->n_factors + kFgWarps - 1) / kFgWarps);
+    const FgTable tab{g->d_ell, g->d_len, {g->ell_base[0], g->ell_base[1], g->ell_base[2]}};
     for (int it = 0; it < n_iters; ++it) {
         if (bp_status st = fg_v2f(g)) return st;
-        if (g->dtype == BP_F32)
-            f2v_kernel<false, float><<<(int)blocks, kFgBlock, smem, g->stream>>>(
-                (const float *)g->n_vf, (float *)g->m_fv, g->d_ptr, g->d_ent, g->C, d, (float)g->fbar);
-        else
-            f2v_kernel<true, int32_t><<<(int)blocks, kFgBlock, smem, g->stream>>>(
-                (const int32_t *)g->n_vf, (int32_t *)g->m_fv, g->d_ptr, g->d_ent, g->C, d, (int32_t)g->fbar);
-        FG_CK(g, cudaGetLastError());
+        const int km = (g->Mp + 31) / 32;
+        cudaError_t e = g->dtype == BP_F32
+            ? (km <= 1 ? launch_f2v<false, float, 1>(g, tab, d) : km <= 2 ? launch_f2v<false, float, 2>(g, tab, d)
+               : km <= 4 ? launch_f2v<false, float, 4>(g, tab, d) : launch_f2v<false, float, 8>(g, tab, d))
+            : (km <= 1 ? launch_f2v<true, int32_t, 1>(g, tab, d) : km <= 2 ? launch_f2v<true, int32_t, 2>(g, tab, d)
+               : km <= 4 ? launch_f2v<true, int32_t, 4>(g, tab, d) : launch_f2v<true, int32_t, 8>(g, tab, d));
+        FG_CK(g, e);
         g->launches += 1;
     }
     return BP_OK;
