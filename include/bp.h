@@ -293,7 +293,9 @@ bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_fac
 bp_status bp_fg_set_unary(bp_factor_graph g, const void *dev_unary);
 /* host_triplets [C][3] distinct (x_0, x_1, x_2) in [0, M); host_vals [C] f
  * (float32) or E (int32); fbar (or the integer Ebar) elsewhere.
- * BP_ERR_POTENTIAL in max mode if some E > Ebar. */
+ * BP_ERR_POTENTIAL in max mode if some E > Ebar.  The table is copied to the
+ * device as three per-slot lists (8 bytes per output label per entry of the
+ * longest list of that slot). */
 bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplets, const void *host_vals,
                            double fbar);
 bp_status bp_fg_reset_messages(bp_factor_graph g);
