@@ -120,6 +120,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_ready(self, timeout=3.0):
+        """Block until the first sample arrives: nvidia-smi's start-up (driver
+        and NVML initialisation) then falls outside the timed region, where it
+        could stall the host's CUDA calls of a wall-clock measurement."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+        return self
+
     def __exit__(self, *a):
         if self.proc:
             time.sleep(0.15)
@@ -270,6 +279,7 @@ def run_ours(args, cfg, rank, world):
     t1 = torch.cuda.Event(enable_timing=True)
     launches0 = G.launches
     with ClockSampler(dev) as clk:
+        clk.wait_ready()
         t0.record(stream)
         for i in range(args.steps):
             step(ev[i])
@@ -291,14 +301,14 @@ def run_ours(args, cfg, rank, world):
     # pinned host memory and reads its MAP back; the upload of step i+1 runs on
     # a copy stream while step i computes (two device staging buffers)
     if not args.no_e2e:
-        n_e = max(1, args.steps // 2)
+        n_e = max(1, args.steps)
         map_host = [torch.empty((cfg.H, cfg.W), dtype=torch.int32).pin_memory() for _ in range(2)]
         bufs = [g_dev, torch.empty_like(g_dev)]
         copy_stream = torch.cuda.Stream()
         ready = [torch.cuda.Event() for _ in range(2)]
         consumed = [None, None]
         torch.cuda.synchronize()
-        clk_e = ClockSampler(dev).__enter__()
+        clk_e = ClockSampler(dev).__enter__().wait_ready()
         e0 = time.perf_counter()
 
         def upload(i):
@@ -410,6 +420,7 @@ def run_batch_workload(args):
         bp.bp_batch_sync(b)
         l0 = bp.bp_batch_launch_count(b)
         with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            clk.wait_ready()
             t = _event_time(stream, step, args.steps)
         bp.bp_batch_sync(b)
         launches = bp.bp_batch_launch_count(b) - l0
