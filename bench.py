@@ -559,13 +559,17 @@ def run_gradient_workload(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     st = wl.make_stereo(cfg)
     cost = torch.from_numpy(st.cost.astype(np.float32)).cuda()
-    G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_F32)
+    gt = torch.as_tensor(st.d_gt, dtype=torch.long).cuda()
+    # the handle orders its work on torch's stream: no host synchronisation
+    # between the library's kernels and torch's
+    G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_F32, stream=torch.cuda.current_stream())
+    beta0 = torch.tensor(cfg.beta, device="cuda")
 
     def step():
         a = torch.tensor(cfg.alpha, requires_grad=True)
         fb = torch.tensor(float(np.exp(-cfg.alpha * cfg.T)), requires_grad=True)
-        be = torch.tensor(cfg.beta, device="cuda", requires_grad=True)
-        loss = autograd.stereo_nll(cost, st.d_gt, a, fb, be, cfg.T, cfg.iters, G, 5)
+        be = beta0.clone().requires_grad_(True)
+        loss = autograd.stereo_nll(cost, gt, a, fb, be, cfg.T, cfg.iters, G, 5)
         loss.backward()
         return float(a.grad)
     for _ in range(args.warmup):

@@ -29,7 +29,8 @@ class BPFunction(torch.autograd.Function):
         bp.bp_iterate(h, n_iters, bp.BP_SUM | bp.BP_LOG | bp.BP_RECORD, bp.BP_SYNC)
         logb = torch.empty_like(logg)
         bp.bp_beliefs(h, logb)
-        bp.bp_sync(h)
+        if not grid.on_current_stream():
+            bp.bp_sync(h)          # the handle's own stream: order it before torch's next work
         ctx.grid = grid
         ctx.T = T
         ctx.table_meta = (table.dtype, table.device)

@@ -429,7 +429,12 @@ class BPGrid:
     def __init__(self, W, H, M, dtype=BP_F32, stream=None):
         self.W, self.H, self.M, self.dtype = W, H, M, dtype
         self.T = None
+        self.stream = stream          # the torch stream the handle orders its work on, or None
         self.h = bp_create(W, H, M, dtype, stream)
+
+    def on_current_stream(self):
+        """True when the handle's work is ordered on torch's current stream."""
+        return self.stream is not None and self.stream == torch.cuda.current_stream()
 
     def close(self):
         if self.h is not None:

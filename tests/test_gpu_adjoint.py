@@ -29,11 +29,11 @@ def test_log_forward_matches_oracle(M, T, schedule):
     H.check_sum_case(g, tab, T, fbar, 7, schedule, log=True)
 
 
-def _gpu_grad(cost, d_gt, alpha, fbar, beta, T, K, every):
+def _gpu_grad(cost, d_gt, alpha, fbar, beta, T, K, every, on_torch_stream=False):
     import torch
     from paper_1010_0012_gb300 import autograd, bp
     Hh, W, M = cost.shape
-    G = bp.BPGrid(W, Hh, M, bp.BP_F32)
+    G = bp.BPGrid(W, Hh, M, bp.BP_F32, stream=torch.cuda.current_stream() if on_torch_stream else None)
     a = torch.tensor(alpha, dtype=torch.float32, requires_grad=True)
     fb = torch.tensor(fbar, dtype=torch.float32, requires_grad=True)
     b = torch.tensor(beta, dtype=torch.float32, device="cuda", requires_grad=True)
@@ -134,3 +134,16 @@ def test_ill_conditioned_beta_gradient_stays_at_the_fp32_floor():
     assert abs(gpu["d_beta"] - fd["d_beta"]) <= floor
     for k in ("d_alpha", "d_fbar"):
         assert abs(gpu[k] - fd[k]) <= GRAD_TOL * max(1.0, abs(fd[k]))
+
+
+def test_grid_on_torch_stream_gives_the_same_gradient():
+    """A grid created on torch's current stream skips the host synchronisation
+    between the library's forward and torch's next operations; the gradient
+    must be the same bit for bit."""
+    import dataclasses
+    cfg = dataclasses.replace(wl.CONFIGS["grid256_m64_grad"], W=48, H=40)
+    st = wl.make_stereo(cfg)
+    args = (st.cost, st.d_gt, 0.9, float(np.float32(np.exp(-0.9 * cfg.T))), 0.1, cfg.T, 12, 4)
+    a = _gpu_grad(*args)
+    b = _gpu_grad(*args, on_torch_stream=True)
+    assert a == b
