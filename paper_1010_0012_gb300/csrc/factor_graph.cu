@@ -29,7 +29,46 @@ struct FgDims {
 };
 
 // ---- variable -> factor: n = unary x the other incoming factor messages ------
-template <bool MIN, typename E>
+// One warp per variable, lane l on labels l, l + 32, ...  Each incoming
+// message is read once per pass; the product over all incoming messages but
+// the k-th comes from prefix and suffix products (min-sum: the total minus the
+// k-th term, exact in integers).  Pass 0 forms the normaliser (sum) or the
+// minimum of every outgoing message, pass 1 writes the normalised messages.
+template <bool MIN, typename E, int D>
+__device__ __forceinline__ void v2f_label(const E *unary, const E *m_fv, const int (&inc)[D], int deg, long long v,
+                                          int x, const FgDims &d, E (&out)[D]) {
+    E m[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) m[j] = j < deg ? m_fv[(long long)inc[j] * d.Mp + x] : (MIN ? E(0) : E(1));
+    const E u = unary[v * d.Mp + x];
+    if (MIN) {
+        E tot = u;
+#pragma unroll
+        for (int j = 0; j < D; ++j) tot += m[j];
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[k] = tot - m[k];
+    } else {
+        // out[k] = u * prod_{j < k} m_j * prod_{j > k} m_j
+        E pre = u;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            out[k] = pre;
+            pre *= m[k];
+        }
+        E suf = E(1);
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+            out[k] *= suf;
+            suf *= m[k];
+        }
+    }
+    if (x >= d.M)
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[k] = MIN ? E(kBig) : E(0);
+}
+
+// D: a bound on the degree of every variable (4, 8 or 16)
+template <bool MIN, typename E, int D>
 __global__ void v2f_kernel(const E *unary, const int32_t *var_ptr, const int32_t *var_inc, const E *m_fv, E *n_vf,
                            FgDims d) {
     const int lane = threadIdx.x & 31;
@@ -37,43 +76,39 @@ __global__ void v2f_kernel(const E *unary, const int32_t *var_ptr, const int32_t
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long v = warp; v < d.n_vars; v += nw) {
         const int p0 = var_ptr[v], deg = var_ptr[v + 1] - p0;
-        // normaliser (sum) or minimum (min-sum) of every outgoing message
-        E acc[kMaxDegree];
+        int inc[D];
 #pragma unroll
-        for (int k = 0; k < kMaxDegree; ++k) acc[k] = MIN ? E(kBig) : E(0);
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int x = lane; x < d.Mp; x += 32) {
-                const E u = unary[v * d.Mp + x];
+        for (int j = 0; j < D; ++j) inc[j] = j < deg ? var_inc[p0 + j] : 0;
+        E acc[D];
 #pragma unroll
-                for (int k = 0; k < kMaxDegree; ++k) {
-                    if (k >= deg) break;
-                    E p = u;
-                    for (int j = 0; j < deg; ++j)
-                        if (j != k) {
-                            const E mj = m_fv[(long long)var_inc[p0 + j] * d.Mp + x];
-                            if (MIN) p += mj; else p *= mj;
-                        }
-                    if (x >= d.M) p = MIN ? E(kBig) : E(0);
-                    if (pass == 0) {
-                        if (MIN) acc[k] = p < acc[k] ? p : acc[k]; else acc[k] += p;
-                    } else {
-                        E out;
-                        if (MIN) out = x < d.M ? p - acc[k] : E(0);
-                        else out = p / acc[k];
-                        n_vf[(long long)var_inc[p0 + k] * d.Mp + x] = out;
-                    }
-                }
+        for (int k = 0; k < D; ++k) acc[k] = MIN ? E(kBig) : E(0);
+        E out[D];
+        for (int x = lane; x < d.Mp; x += 32) {
+            v2f_label<MIN, E, D>(unary, m_fv, inc, deg, v, x, d, out);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (MIN) acc[k] = out[k] < acc[k] ? out[k] : acc[k]; else acc[k] += out[k];
             }
-            if (pass == 0)
+        }
 #pragma unroll
-                for (int k = 0; k < kMaxDegree; ++k) {
-                    if (k >= deg) break;
+        for (int k = 0; k < D; ++k) {
+            if (k >= deg) break;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const E y = __shfl_xor_sync(0xffffffffu, acc[k], o);
-                        if (MIN) acc[k] = y < acc[k] ? y : acc[k]; else acc[k] += y;
-                    }
-                }
+            for (int o = 16; o > 0; o >>= 1) {
+                const E y = __shfl_xor_sync(0xffffffffu, acc[k], o);
+                if (MIN) acc[k] = y < acc[k] ? y : acc[k]; else acc[k] += y;
+            }
+        }
+        for (int x = lane; x < d.Mp; x += 32) {
+            v2f_label<MIN, E, D>(unary, m_fv, inc, deg, v, x, d, out);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (k >= deg) break;
+                E o;
+                if (MIN) o = x < d.M ? out[k] - acc[k] : E(0);
+                else o = out[k] / acc[k];
+                n_vf[(long long)inc[k] * d.Mp + x] = o;
+            }
         }
     }
 }
@@ -294,6 +329,7 @@ thread_local std::string g_fg_err;
 
 struct bp_fg_ctx {
     int n_vars = 0, n_factors = 0, M = 0, Mp = 0;
+    int max_degree = 0;          // largest number of factors of one variable
     bp_dtype dtype = BP_F32;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -349,6 +385,12 @@ static cudaError_t launch_f2v(bp_factor_graph g, const FgTable &tab, const FgDim
     return cudaGetLastError();
 }
 
+template <bool MIN, typename E, int D>
+static void launch_v2f(bp_factor_graph g, const FgDims &d) {
+    v2f_kernel<MIN, E, D><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
+        (const E *)g->unary, g->var_ptr, g->var_inc, (const E *)g->m_fv, (E *)g->n_vf, d);
+}
+
 extern "C" {
 
 const char *bp_fg_last_error(bp_factor_graph g) { return g ? g->err.c_str() : g_fg_err.c_str(); }
@@ -387,6 +429,7 @@ bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_fac
     }
     bp_factor_graph g = new bp_fg_ctx();
     g->n_vars = n_vars; g->n_factors = n_factors; g->M = M; g->Mp = (M + 3) & ~3; g->dtype = dtype;
+    for (int v = 0; v < n_vars; ++v) g->max_degree = std::max(g->max_degree, deg[v]);
     if (cuda_stream) g->stream = (cudaStream_t)cuda_stream;
     else if (cudaStreamCreateWithFlags(&g->stream, cudaStreamDefault) != cudaSuccess) {
         delete g;
@@ -540,12 +583,16 @@ static bp_status fg_prepare(bp_factor_graph g, int mode) {
 
 static bp_status fg_v2f(bp_factor_graph g) {
     const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
-    if (g->dtype == BP_F32)
-        v2f_kernel<false, float><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
-            (const float *)g->unary, g->var_ptr, g->var_inc, (const float *)g->m_fv, (float *)g->n_vf, d);
-    else
-        v2f_kernel<true, int32_t><<<warp_grid(g->n_vars), 256, 0, g->stream>>>(
-            (const int32_t *)g->unary, g->var_ptr, g->var_inc, (const int32_t *)g->m_fv, (int32_t *)g->n_vf, d);
+    const int D = g->max_degree <= 4 ? 4 : g->max_degree <= 8 ? 8 : 16;
+    if (g->dtype == BP_F32) {
+        if (D == 4) launch_v2f<false, float, 4>(g, d);
+        else if (D == 8) launch_v2f<false, float, 8>(g, d);
+        else launch_v2f<false, float, 16>(g, d);
+    } else {
+        if (D == 4) launch_v2f<true, int32_t, 4>(g, d);
+        else if (D == 8) launch_v2f<true, int32_t, 8>(g, d);
+        else launch_v2f<true, int32_t, 16>(g, d);
+    }
     FG_CK(g, cudaGetLastError());
     g->launches += 1;
     return BP_OK;

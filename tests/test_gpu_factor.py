@@ -93,3 +93,30 @@ def test_factor_rejects_energy_above_ebar_and_bad_factors():
     with pytest.raises(bp.BPError) as ei:
         bp.bp_fg_create(5, 4, [(0, 1, 1)], bp.BP_I32)
     assert ei.value.status == bp.BP_ERR_ARG
+
+
+@pytest.mark.parametrize("hub_degree", [5, 9, 16])
+def test_factor_hub_variable_degrees(hub_degree):
+    """One variable in hub_degree factors (the largest degree bound the
+    variable-to-factor kernel is compiled for is 16), the others in few:
+    sum-product within 1e-5 and min-sum exact against the dense oracle."""
+    import oracle
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(hub_degree)
+    M, nv = 12, 3 + 2 * hub_degree
+    fs = np.array([(0, 1 + 2 * i, 2 + 2 * i) for i in range(hub_degree)] + [(1, 2, 3)], np.int32)
+    trip = random_triplets(M, 150, rng)
+    g = rng.uniform(0.05, 1.0, (nv, M)).astype(np.float32)
+    vals = rng.uniform(0.2, 3.0, len(trip)).astype(np.float32)
+    bel, mp, msg = _gpu(g, fs, trip, vals, 0.15, 4, bp.BP_F32)
+    F = factor.dense_table(trip, vals.astype(np.float64), 0.15, M)
+    m64, b64 = factor.sum_product(g.astype(np.float64), fs, F, 4)
+    assert H.node_rel_err(bel, b64) <= H.REL_TOL
+    E = rng.integers(0, 25, (nv, M)).astype(np.int32)
+    vi = rng.integers(0, 13, len(trip)).astype(np.int32)
+    bel, mp, msg = _gpu(E, fs, trip, vi, 12, 4, bp.BP_I32)
+    V = factor.dense_table(trip, vi.astype(np.int64), 12, M, dtype=np.int64)
+    m64, b64 = factor.min_sum(E.astype(np.int64), fs, V, 4)
+    np.testing.assert_array_equal(msg.astype(np.int64), m64)
+    np.testing.assert_array_equal(bel.astype(np.int64), b64)
+    np.testing.assert_array_equal(mp, oracle.map_labels(b64, maximise=False))
