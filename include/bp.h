@@ -145,7 +145,10 @@ bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind);
 bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map);
 
 /* Copy the current message planes out / in ([4][H][W][M], dtype of the
- * handle; log-messages in log mode).  Used to checkpoint or inject a state. */
+ * handle).  Float32 messages cross this boundary linear (normalised) in every
+ * mode: after log-mode iterations bp_get_messages returns exp of the
+ * log-domain state, and bp_set_messages installs a linear state.  Used to
+ * checkpoint or inject a state. */
 bp_status bp_get_messages(bp_handle h, void *dev_planes);
 bp_status bp_set_messages(bp_handle h, const void *dev_planes);
 

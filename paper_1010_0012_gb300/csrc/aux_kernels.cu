@@ -199,7 +199,7 @@ __global__ void beliefs_f32_kernel(const float *g, const float *planes, GridDims
                 float a = g[node * Mp + x];
                 for (int s = 0; s < 4; ++s)
                     if (has[s]) a += planes[s * d.plane + node * Mp + x];
-                b = expf(a - amax);
+                b = exp2f(a - amax);
             } else {
                 b = g[node * Mp + x];
                 for (int s = 0; s < 4; ++s)
@@ -208,7 +208,7 @@ __global__ void beliefs_f32_kernel(const float *g, const float *planes, GridDims
             Z += b;
         }
         for (int o = 16; o > 0; o >>= 1) Z += __shfl_xor_sync(0xffffffffu, Z, o);
-        const float logZ = log_domain ? amax + logf(Z) : 0.f;
+        const float logZ = log_domain ? amax + log2f(Z) : 0.f;   // base 2
         float best = -3.0e38f;
         int besti = 0x7fffffff;
         for (int x = lane; x < M; x += 32) {
@@ -217,7 +217,7 @@ __global__ void beliefs_f32_kernel(const float *g, const float *planes, GridDims
                 float a = g[node * Mp + x];
                 for (int s = 0; s < 4; ++s)
                     if (has[s]) a += planes[s * d.plane + node * Mp + x];
-                b = a - logZ;
+                b = (a - logZ) * 0.693147180559945309f;   // natural log-belief
             } else {
                 b = g[node * Mp + x];
                 for (int s = 0; s < 4; ++s)
@@ -274,6 +274,7 @@ __global__ void pad_f32_kernel(const float *src, float *dst, long long nodes, in
             v = src[node * M + x];
             if (lg == 1) v = logf(v);
             else if (lg == 2) v = expf(v);
+            else if (lg == 3) v *= 1.44269504088896341f;   // natural log -> base-2 log
         }
         dst[i] = v;
     }
@@ -442,25 +443,29 @@ cudaError_t launch_beliefs_i32(const int32_t *e, const int32_t *planes, GridDims
 }  // namespace bpg
 
 // ---- linear <-> log conversions ------------------------------------------------
+// The log domain of the library is base 2 throughout (messages, log g, the
+// recorded states): the log-domain kernels then take h from one hardware 2^x
+// of an exact argument and store one hardware log2.  Natural logs appear only
+// at the boundary (bp_set_unary_log, log-beliefs, gradients).
 namespace bpg {
 namespace {
 __global__ void convert_kernel(float *p, long long rows, int M, int Mp, int to_log) {
     const long long n = rows * Mp;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % Mp);
-        p[i] = x < M ? (to_log ? logf(p[i]) : expf(p[i])) : 0.f;
+        p[i] = x < M ? (to_log ? log2f(p[i]) : exp2f(p[i])) : 0.f;
     }
 }
 __global__ void log_copy_kernel(const float *g, float *lg, long long nodes, int M, int Mp) {
     const long long n = nodes * Mp;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(i % Mp);
-        lg[i] = x < M ? logf(g[i]) : 0.f;
+        lg[i] = x < M ? log2f(g[i]) : 0.f;
     }
 }
 __global__ void convert_dense_kernel(float *p, long long n, int to_log) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = to_log ? logf(p[i]) : expf(p[i]);
+        p[i] = to_log ? log2f(p[i]) : exp2f(p[i]);
 }
 }  // namespace
 

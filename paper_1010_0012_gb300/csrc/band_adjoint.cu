@@ -12,8 +12,11 @@
 //   dw(d)    += sum_{x_j} nu(x_j) h(x_j + d)                           (= dL/df(d))
 //   dfbar    += S sum_x nu(x) - sum_d dw(d)   (fbar enters u directly and through w)
 // The common factor exp(A) of h, u, Z and nu cancels in every product above.
-// h is recomputed exactly as the forward kernel computes it; delta / u uses
-// the hardware approximate division (2 ulp; u > 0 is a normal float here).
+// The states and log g are base-2 logs (the library's log domain): h and the
+// belief softmax are computed with 2^x exactly as the forward kernel does,
+// while every adjoint (delta, nu, da, dL/d log g) is a derivative with
+// respect to natural logs, the units of the caller's log g and log-beliefs.
+// delta / u uses the hardware approximate division (2 ulp; u > 0 is normal).
 //
 // One kernel launch reverses one synchronous iteration for every node; the
 // per-block sums of dw and dfbar go to a scratch row per (iteration, block),
@@ -118,7 +121,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
             float S = 0.f, Z = 0.f;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                h[k] = lab_ok[k] ? exp_shifted(h[k] - amax) : 0.f;   // as the forward kernel
+                h[k] = lab_ok[k] ? exp2_hw(h[k] - amax) : 0.f;   // as the forward kernel
                 S += h[k];
                 Z = fmaf(h[k], cz[k], Z);
             }
@@ -285,7 +288,7 @@ __global__ void beliefs_log_adjoint_kernel(const float *logg, const float *ell, 
             float av = logg[node * Mp + x];
             for (int s = 0; s < 4; ++s)
                 if (has[s]) av += ell[s * d.plane + node * Mp + x];
-            Z += expf(av - amax);
+            Z += exp2f(av - amax);
         }
         for (int o = 16; o > 0; o >>= 1) Z += __shfl_xor_sync(0xffffffffu, Z, o);
         for (int x = lane; x < Mp; x += 32) {
@@ -294,7 +297,7 @@ __global__ void beliefs_log_adjoint_kernel(const float *logg, const float *ell, 
                 float av = logg[node * Mp + x];
                 for (int s = 0; s < 4; ++s)
                     if (has[s]) av += ell[s * d.plane + node * Mp + x];
-                da = dlogb[node * M + x] - expf(av - amax) / Z * D;
+                da = dlogb[node * M + x] - exp2f(av - amax) / Z * D;
             }
             dlogg[node * Mp + x] = da;
             for (int s = 0; s < 4; ++s)

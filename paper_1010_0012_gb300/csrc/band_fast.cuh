@@ -6,13 +6,6 @@
 // forms the four products h of Eq. 5 in registers, and writes the four outgoing
 // messages (4 x Mp words) straight into the neighbours' incoming planes:
 //
-// The log-domain form (messages and unary stored as natural logs) takes h from
-// exp(log g + sum of log-messages - their maximum) and stores log m.  The log
-// is the hardware approximation __logf (absolute error about 2^-21 near 1,
-// a few ulp elsewhere); the exp is exp_shifted below, accurate to a few ulp
-// over the whole range (the error of __expf grows with |x|, which shows in
-// ill-conditioned gradients).
-//
 //   sum-product (Eq. 7):
 //     S      = sum_x h(x)                        (group shuffle reduction)
 //     B(x_j) = sum_{|d| <= T} [f(d) - fbar] h(x_j + d)   (band; halo via shuffles)
@@ -26,6 +19,12 @@
 //   sum_{x_j} B(x_j) = sum_{x_i} h(x_i) c(x_i),  c(x_i) = sum of f(d) - fbar over
 //   the d that keep x_j = x_i - d inside [0, M),
 // so sum_x u = sum_x h(x) (c(x) + M fbar), reduced together with S.
+//
+// The log-domain form keeps messages and log g as base-2 logs: h is
+// 2^(log2 g + sum of log2-messages - their maximum), one hardware ex2 of an
+// exact argument, and the stored message is the hardware log2 of m (absolute
+// error about 2^-22).  The results are the linear form's within about 1e-6.
+
 #pragma once
 
 #include <cuda_runtime.h>
@@ -84,22 +83,13 @@ __device__ __forceinline__ int32_t min_vec(const int32_t (&v)[V]) {
     return r;
 }
 
-// e^x for x <= 0 (the max-shifted exponents of the log-domain kernels) within a
-// few ulp.  x log2(e) is split exactly into head + tail (the FMA TwoProduct of
-// Ogita, Rump and Oishi, SIAM J. Sci. Comput. 2005, plus the tail of the
-// constant log2(e) itself); the head goes to the hardware 2^y
-// (ex2.approx.ftz, a 2-ulp approximation whose input is now exact), the tail
-// to the first-order factor 1 + tail ln 2.  Results below 2^-126 flush to 0.
-__device__ __forceinline__ float exp_shifted(float x) {
-    constexpr float kLog2eHi = 1.44269502162933349609375f;   // nearest float to log2(e)
-    constexpr float kLog2eLo = 1.9259629911266175e-08f;      // log2(e) - kLog2eHi
-    constexpr float kLn2 = 0.693147180559945309f;
-    const float hi = x * kLog2eHi;
-    float lo = fmaf(x, kLog2eHi, -hi);
-    lo = fmaf(x, kLog2eLo, lo);
+// 2^x by the hardware approximation (ex2.approx.ftz: about 2 ulp; results
+// below 2^-126 flush to 0).  The log-domain kernels work in base 2, so the
+// max-shifted argument is exact and this is the whole exp.
+__device__ __forceinline__ float exp2_hw(float x) {
     float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(hi));
-    return fmaf(r, lo * kLn2, r);
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // ------------------------------------------------------- group reductions ----
@@ -283,7 +273,7 @@ struct SumBand {
                 }
                 amax = group_max<L>(amax);
 #pragma unroll
-                for (int k = 0; k < V; ++k) h[k] = lab_ok[k] ? exp_shifted(h[k] - amax) : 0.f;
+                for (int k = 0; k < V; ++k) h[k] = lab_ok[k] ? exp2_hw(h[k] - amax) : 0.f;
             }
 
             float S = 0.f, Z = 0.f;
@@ -306,7 +296,7 @@ struct SumBand {
 #pragma unroll
                 for (int d = -T; d <= T; ++d) acc = fmaf(w[d + T], win[T + k + d], acc);
                 const float mv = fmaf(acc, inv, base_term);
-                o[k] = lab_ok[k] ? (LOG ? __logf(mv) : mv) : 0.f;
+                o[k] = lab_ok[k] ? (LOG ? __log2f(mv) : mv) : 0.f;
             }
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
         }

@@ -89,7 +89,7 @@ static bp_status materialize(bp_ctx *h, bool want_log) {
         if (h->dtype == BP_I32) {
             BP_CK(h, launch_fill_messages_i32((int32_t *)h->msg[h->cur], rows, h->M, h->Mp, 0, h->stream));
         } else {
-            const float v = want_log ? -logf((float)h->M) : 1.0f / (float)h->M;
+            const float v = want_log ? -log2f((float)h->M) : 1.0f / (float)h->M;   // log domain: base 2
             BP_CK(h, launch_fill_messages_f32((float *)h->msg[h->cur], rows, h->M, h->Mp, v, h->stream));
         }
         h->launches += 1;
@@ -418,7 +418,7 @@ bp_status bp_set_unary_log(bp_handle h, const float *dev_logg) {
     if (bp_status st = bpg_check_device(h)) return st;
     const long long nodes = (long long)h->W * h->H;
     if (bp_status st = ensure_buffer(h, (void **)&h->log_unary, (size_t)nodes * h->Mp * 4, "log unary")) return st;
-    BP_CK(h, launch_pad_copy_f32(dev_logg, h->log_unary, nodes, h->M, h->Mp, 0, h->stream));
+    BP_CK(h, launch_pad_copy_f32(dev_logg, h->log_unary, nodes, h->M, h->Mp, 3, h->stream));   // to base 2
     BP_CK(h, launch_pad_copy_f32(dev_logg, (float *)h->unary, nodes, h->M, h->Mp, 2, h->stream));
     h->launches += 2;
     h->have_unary = true;
