@@ -208,7 +208,8 @@ __device__ __forceinline__ void ld_msg(int32_t (&v)[V], const int32_t *p) {
 // LOG = false: linear messages, g is the unary.  LOG = true: log-messages,
 // g holds log g; h is formed as exp(log h - max log h), which leaves the
 // normalised result unchanged.
-template <int L, int C, int T, bool LOG, bool COH>
+// FULL: every padded label is a label (M == Mp), so the label masks vanish
+template <int L, int C, int T, bool LOG, bool COH, bool FULL = false>
 struct SumBand {
     static constexpr int V = 4 * C;
     float w[2 * T + 1];
@@ -268,12 +269,12 @@ struct SumBand {
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         if (u != t) s += m[u][k];
-                    h[k] = lab_ok[k] ? s : kLogNone;
+                    h[k] = (FULL || lab_ok[k]) ? s : kLogNone;
                     amax = fmaxf(amax, h[k]);
                 }
                 amax = group_max<L>(amax);
 #pragma unroll
-                for (int k = 0; k < V; ++k) h[k] = lab_ok[k] ? exp2_hw(h[k] - amax) : 0.f;
+                for (int k = 0; k < V; ++k) h[k] = (FULL || lab_ok[k]) ? exp2_hw(h[k] - amax) : 0.f;
             }
 
             float S = 0.f, Z = 0.f;
@@ -296,18 +297,18 @@ struct SumBand {
 #pragma unroll
                 for (int d = -T; d <= T; ++d) acc = fmaf(w[d + T], win[T + k + d], acc);
                 const float mv = fmaf(acc, inv, base_term);
-                o[k] = lab_ok[k] ? (LOG ? __log2f(mv) : mv) : 0.f;
+                o[k] = (FULL || lab_ok[k]) ? (LOG ? __log2f(mv) : mv) : 0.f;
             }
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
         }
     }
 };
 
-template <int L, int C, int T, bool LOG>
+template <int L, int C, int T, bool LOG, bool FULL = false>
 __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
     constexpr int GPB = kBlock / L;
     const int grp = threadIdx.x / L;
-    SumBand<L, C, T, LOG, false> band;
+    SumBand<L, C, T, LOG, false, FULL> band;
     band.setup(a.w, a.fbar, a.d.M, threadIdx.x & (L - 1));
     const int W = a.d.W;
     const int nslots = num_slots(W, a.d.H, a.parity);

@@ -10,8 +10,14 @@ struct LogTag {
     static const void *get() { return (const void *)band_sum_kernel<L, C, T, true>; }
 };
 
+// M == Mp (every power-of-two label count): the form without label masks
+struct LogFullTag {
+    template <int L, int C, int T>
+    static const void *get() { return (const void *)band_sum_kernel<L, C, T, true, true>; }
+};
+
 cudaError_t launch_band_log(const BandArgsF &a, Layout lay, int blocks, cudaStream_t s) {
-    return launch_fast<LogTag>(a, lay, blocks, s);
+    return a.d.M == a.d.Mp ? launch_fast<LogFullTag>(a, lay, blocks, s) : launch_fast<LogTag>(a, lay, blocks, s);
 }
 
 }  // namespace bpg
