@@ -324,7 +324,8 @@ __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
 // min_x u(x) = E(0) + min_x h(x) exactly: the pair (x*, x*) with h(x*) minimal
 // is in the band, every band term is >= E(0) + min h, and Ebar >= E(0).  The
 // second reduction is then skipped (`zero_min`).
-template <int L, int C, int T, bool COH>
+// FULL: M == Mp, every padded label is a label and the label masks vanish
+template <int L, int C, int T, bool COH, bool FULL = false>
 struct MinBand {
     static constexpr int V = 4 * C;
     static constexpr int VP = V / 2;            // label pairs per lane (packed form)
@@ -393,7 +394,7 @@ struct MinBand {
                 const uint32_t term = (r & 1) ? odd[(r - 1) / 2] : win[r / 2];
                 a = __viaddmin_s16x2(wp[d + T], term, a);
             }
-            acc[k] = (a & keep[k]) | (flat & ~keep[k]);   // labels >= M: Ebar', never below the minimum
+            acc[k] = FULL ? a : (a & keep[k]) | (flat & ~keep[k]);   // labels >= M: Ebar', never below the minimum
         }
         int32_t umin;
         if (zero_min) {
@@ -407,7 +408,7 @@ struct MinBand {
         const uint32_t sub = (uint32_t)umin * 0x10001u;
 #pragma unroll
         for (int k = 0; k < VP; ++k) {
-            const uint32_t o = (acc[k] - sub) & keep[k];    // no borrow: every half >= umin
+            const uint32_t o = FULL ? acc[k] - sub : (acc[k] - sub) & keep[k];   // no borrow: every half >= umin
             u[2 * k] = (int32_t)(o & 0xffffu);
             u[2 * k + 1] = (int32_t)(o >> 16);
         }
@@ -423,11 +424,11 @@ struct MinBand {
             int32_t b = flat;
 #pragma unroll
             for (int d = -T; d <= T; ++d) b = __viaddmin_s32(w[d + T], win[T + k + d], b);
-            u[k] = lab_ok[k] ? b : kIntBig;
+            u[k] = (FULL || lab_ok[k]) ? b : kIntBig;
         }
         const int32_t umin = zero_min ? w[T] + hmin : group_min<L>(min_vec<V>(u));
 #pragma unroll
-        for (int k = 0; k < V; ++k) u[k] = lab_ok[k] ? u[k] - umin : 0;
+        for (int k = 0; k < V; ++k) u[k] = (FULL || lab_ok[k]) ? u[k] - umin : 0;
     }
 
     __device__ __forceinline__ void node(const int32_t *e, const int32_t *in, int32_t *out, int W, int H, int Mp,
@@ -446,7 +447,7 @@ struct MinBand {
         // h of direction t is that total minus the message from side t
         int32_t tot[V];
 #pragma unroll
-        for (int k = 0; k < V; ++k) tot[k] = lab_ok[k] ? ev[k] + m[0][k] + m[1][k] + m[2][k] + m[3][k] : kIntBig;
+        for (int k = 0; k < V; ++k) tot[k] = (FULL || lab_ok[k]) ? ev[k] + m[0][k] + m[1][k] + m[2][k] + m[3][k] : kIntBig;
 
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -470,11 +471,11 @@ struct MinBand {
     }
 };
 
-template <int L, int C, int T>
+template <int L, int C, int T, bool FULL = false>
 __global__ void __launch_bounds__(kBlock) band_min_kernel(const BandArgsI a) {
     constexpr int GPB = kBlock / L;
     const int grp = threadIdx.x / L;
-    MinBand<L, C, T, false> band;
+    MinBand<L, C, T, false, FULL> band;
     band.setup(a.w, a.ebar, a.d.M, threadIdx.x & (L - 1), a.zero_min != 0, a.packed16 != 0);
     const int W = a.d.W;
     const int nslots = num_slots(W, a.d.H, a.parity);
