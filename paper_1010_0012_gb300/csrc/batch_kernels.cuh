@@ -75,7 +75,8 @@ __device__ __forceinline__ bool batch_grid_barrier(unsigned *count, unsigned *ge
 
 // parity < 0: synchronous (read msg[src], write msg[src ^ 1]); parity 0/1:
 // red-black half-step in place on msg[src], slots as in slot_node.
-template <int L, int C, int T, bool MIN, bool RB>
+// FULL: every MRF of the batch has M == Mp (min-sum: no padded-label masks)
+template <int L, int C, int T, bool MIN, bool RB, bool FULL>
 __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int node0, int count, int src,
                                            int parity_rt) {
     const int parity = RB ? parity_rt : -1;
@@ -89,7 +90,7 @@ __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int n
     const void *in = m->msg[src];
     void *out = parity < 0 ? m->msg[src ^ 1] : m->msg[src];
     if (MIN) {
-        MinBand<L, C, T, true> b;
+        MinBand<L, C, T, true, FULL> b;
         b.setup(m->wi, m->ebar, m->M, q, m->zero_min != 0, m->packed16 != 0);
         for (int base = 0; base < count; base += GPB) {
             int r = 0, c = 0;
@@ -121,49 +122,49 @@ __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int n
     }
 }
 
-template <int L, int C, bool MIN, bool RB>
+template <int L, int C, bool MIN, bool RB, bool FULL>
 __device__ __forceinline__ void batch_item_t(const BatchMrf *__restrict__ m, int node0, int count, int src,
                                              int parity) {
     switch (m->T) {
-        case 0: batch_item<L, C, 0, MIN, RB>(m, node0, count, src, parity); break;
-        case 1: batch_item<L, C, 1, MIN, RB>(m, node0, count, src, parity); break;
-        case 2: batch_item<L, C, 2, MIN, RB>(m, node0, count, src, parity); break;
-        case 3: batch_item<L, C, 3, MIN, RB>(m, node0, count, src, parity); break;
-        case 4: batch_item<L, C, 4, MIN, RB>(m, node0, count, src, parity); break;
-        case 5: batch_item<L, C, 5, MIN, RB>(m, node0, count, src, parity); break;
-        case 6: batch_item<L, C, 6, MIN, RB>(m, node0, count, src, parity); break;
-        case 7: batch_item<L, C, 7, MIN, RB>(m, node0, count, src, parity); break;
-        default: batch_item<L, C, 8, MIN, RB>(m, node0, count, src, parity); break;
+        case 0: batch_item<L, C, 0, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 1: batch_item<L, C, 1, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 2: batch_item<L, C, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 3: batch_item<L, C, 3, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 4: batch_item<L, C, 4, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 5: batch_item<L, C, 5, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 6: batch_item<L, C, 6, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        case 7: batch_item<L, C, 7, MIN, RB, FULL>(m, node0, count, src, parity); break;
+        default: batch_item<L, C, 8, MIN, RB, FULL>(m, node0, count, src, parity); break;
     }
 }
 
 // Family 1: the fewest labels per lane (C = 1 up to 128 labels);
 // family 2: two 4-label chunks per lane.  Padded label counts 16..256.
-template <int FAM, bool MIN, bool RB>
+template <int FAM, bool MIN, bool RB, bool FULL>
 __device__ __forceinline__ void batch_dispatch(const BatchMrf *__restrict__ m, int node0, int count, int src,
                                                int parity) {
     if (FAM == 1) {
         switch (m->Mp) {
-            case 16: batch_item_t<4, 1, MIN, RB>(m, node0, count, src, parity); break;
-            case 32: batch_item_t<8, 1, MIN, RB>(m, node0, count, src, parity); break;
-            case 64: batch_item_t<16, 1, MIN, RB>(m, node0, count, src, parity); break;
-            case 128: batch_item_t<32, 1, MIN, RB>(m, node0, count, src, parity); break;
-            default: batch_item_t<32, 2, MIN, RB>(m, node0, count, src, parity); break;
+            case 16: batch_item_t<4, 1, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            case 32: batch_item_t<8, 1, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            case 64: batch_item_t<16, 1, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            case 128: batch_item_t<32, 1, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            default: batch_item_t<32, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
         }
     } else {
         switch (m->Mp) {
-            case 16: batch_item_t<2, 2, MIN, RB>(m, node0, count, src, parity); break;
-            case 32: batch_item_t<4, 2, MIN, RB>(m, node0, count, src, parity); break;
-            case 64: batch_item_t<8, 2, MIN, RB>(m, node0, count, src, parity); break;
-            case 128: batch_item_t<16, 2, MIN, RB>(m, node0, count, src, parity); break;
-            default: batch_item_t<32, 2, MIN, RB>(m, node0, count, src, parity); break;
+            case 16: batch_item_t<2, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            case 32: batch_item_t<4, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            case 64: batch_item_t<8, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            case 128: batch_item_t<16, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
+            default: batch_item_t<32, 2, MIN, RB, FULL>(m, node0, count, src, parity); break;
         }
     }
 }
 
 // RB: the red-black form (two in-place half-steps per iteration), compiled
 // separately so that the synchronous batch kernel keeps its registers.
-template <int FAM, bool MIN, bool RB>
+template <int FAM, bool MIN, bool RB, bool FULL = false>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
     __shared__ unsigned long long s_ticket[2];
     const int phases = RB ? 2 : 1;
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
         while (ticket < first + n_items) {
             if (threadIdx.x == 0) s_ticket[slot ^ 1] = atomicAdd(a.tickets, 1ull);
             const BatchItem item = a.items[ticket - first];
-            batch_dispatch<FAM, MIN, RB>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
+            batch_dispatch<FAM, MIN, RB, FULL>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
             __syncthreads();
             slot ^= 1;
             ticket = s_ticket[slot];

@@ -25,7 +25,7 @@ namespace bpg {
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
 int batch_max_blocks_sum(int family, bool redblack = false);
-int batch_max_blocks_min(int family, bool redblack = false);
+int batch_max_blocks_min(int family, bool redblack = false, bool full = false);
 
 int batch_lanes_per_node(int family, int Mp) {
     if (family == 1) return Mp >= 256 ? 32 : Mp / 4;
@@ -69,6 +69,7 @@ struct bp_batch_ctx {
     int *d_status = nullptr;
     int family = 1;
     int tile_words = 16384;
+    bool all_full = false;       // every MRF has M == Mp
     int items_family = 0, items_tile = 0;
     int cur = 0;
     bool uniform_pending = true;
@@ -132,7 +133,8 @@ static bp_status build_items(bp_batch b) {
 }
 
 static int batch_blocks(bp_batch b) {
-    const int maxb = b->dtype == BP_I32 ? batch_max_blocks_min(b->family) : batch_max_blocks_sum(b->family);
+    const int maxb = b->dtype == BP_I32 ? batch_max_blocks_min(b->family, false, b->all_full)
+                                        : batch_max_blocks_sum(b->family);
     return std::max(1, std::min(maxb, b->n_items));
 }
 
@@ -146,6 +148,7 @@ static cudaError_t issue_batch(bp_batch b, int n_iters, int cur) {
     a.bar_count = b->d_bar;
     a.bar_gen = b->d_bar + kBatchGenWord;
     a.tickets = reinterpret_cast<unsigned long long *>(b->d_bar + kBatchTicketWord);
+    a.full = b->all_full ? 1 : 0;
     a.extra_arrivals = b->extra_arrivals;
     a.limit_ns = b->limit_ns;
     a.status = b->d_status;
@@ -302,6 +305,8 @@ bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void 
             st = bfail(nullptr, BP_ERR_CUDA, "bp_batch_create: descriptor upload failed");
     }
     if (st == BP_OK) {
+        b->all_full = true;
+        for (const MrfHost &m : b->mrfs) b->all_full = b->all_full && m.M == m.Mp;
         st = build_items(b);
         if (st) g_batch_err = b->err;
     }

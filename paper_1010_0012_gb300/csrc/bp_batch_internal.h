@@ -38,6 +38,7 @@ struct BatchArgs {
     int n_iters;
     int start_buf;              // synchronous: iteration t reads msg[(start_buf + t) & 1]
     int redblack;               // 1: two in-place half-steps per iteration on msg[start_buf]
+    int full;                   // host-side choice: every MRF has M == Mp (kernel variant without label masks)
     unsigned *bar_count;        // grid barrier: arrivals, generation
     unsigned *bar_gen;
     unsigned long long *tickets;   // work counter, zero at launch: ticket k is item k % n_items of step k / n_items

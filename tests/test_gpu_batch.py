@@ -11,11 +11,11 @@ from tests import gpu_helpers as H
 pytestmark = pytest.mark.gpu
 
 
-def _mrfs(n=7, seed=3):
+def _mrfs(n=7, seed=3, label_counts=(16, 32, 64, 100, 128, 256)):
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
-        M = int(rng.choice([16, 32, 64, 100, 128, 256]))
+        M = int(rng.choice(label_counts))
         T = int(rng.integers(0, 9))
         W, Hh = int(rng.integers(3, 23)), int(rng.integers(2, 17))
         alpha = float(rng.uniform(0.25, 1.0))
@@ -200,3 +200,12 @@ def test_batch_rejects_potential_below_fbar_in_max_mode():
     with pytest.raises(bp.BPError) as ei:
         bp.bp_batch_create([(un, np.array([0, 9, 0], dtype=np.int32), 1, 5)], bp.BP_I32)
     assert ei.value.status == bp.BP_ERR_POTENTIAL
+
+
+@pytest.mark.parametrize("family", [1, 2])
+def test_batch_min_power_of_two_labels_bit_exact(family):
+    """Every MRF with M a power of two: the batch runs the kernel variant
+    without padded-label masks (the others above include M = 100)."""
+    mrfs = _mrfs(n=6, seed=11, label_counts=(16, 32, 64, 128, 256))
+    res, _ = _run_batch(mrfs, H.bp().BP_I32, 6, family=family, tile=2048)
+    _check_min(mrfs, res, 6)
