@@ -75,7 +75,7 @@ __device__ __forceinline__ bool batch_grid_barrier(unsigned *count, unsigned *ge
 
 // parity < 0: synchronous (read msg[src], write msg[src ^ 1]); parity 0/1:
 // red-black half-step in place on msg[src], slots as in slot_node.
-// FULL: every MRF of the batch has M == Mp (min-sum: no padded-label masks)
+// FULL: every MRF of the batch has M == Mp (no padded-label masks)
 template <int L, int C, int T, bool MIN, bool RB, bool FULL>
 __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int node0, int count, int src,
                                            int parity_rt) {
@@ -105,7 +105,7 @@ __device__ __forceinline__ void batch_item(const BatchMrf *__restrict__ m, int n
             b.node((const int32_t *)un, (const int32_t *)in, (int32_t *)out, W, H, Mp, plane, r, c, valid);
         }
     } else {
-        SumBand<L, C, T, false, true> b;
+        SumBand<L, C, T, false, true, FULL> b;
         b.setup(m->wf, m->fbar, m->M, q);
         for (int base = 0; base < count; base += GPB) {
             int r = 0, c = 0;

@@ -4,12 +4,17 @@
 
 namespace bpg {
 
-const void *batch_sum_kernel_f1();   // batch_sum_f1.cu
-const void *batch_sum_kernel_f2();   // batch_sum_f2.cu
-const void *batch_sum_kernel_rb();   // batch_sum_rb.cu
+const void *batch_sum_kernel_f1();        // batch_sum_f1.cu
+const void *batch_sum_kernel_f2();        // batch_sum_f2.cu
+const void *batch_sum_kernel_f1_full();   // batch_sum_f1_full.cu
+const void *batch_sum_kernel_f2_full();   // batch_sum_f2_full.cu
+const void *batch_sum_kernel_rb();        // batch_sum_rb.cu
 
-static const void *batch_sum_fn(int family, bool redblack = false) {
+// full: every MRF has M == Mp, the variant without padded-label masks (same
+// launch bounds, so the same two resident blocks per SM)
+static const void *batch_sum_fn(int family, bool redblack = false, bool full = false) {
     if (redblack) return batch_sum_kernel_rb();
+    if (full) return family == 2 ? batch_sum_kernel_f2_full() : batch_sum_kernel_f1_full();
     return family == 2 ? batch_sum_kernel_f2() : batch_sum_kernel_f1();
 }
 
@@ -24,11 +29,11 @@ cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStr
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     void *args[] = {const_cast<BatchArgs *>(&a)};
-    return cudaLaunchKernelExC(&cfg, batch_sum_fn(family, a.redblack != 0), args);
+    return cudaLaunchKernelExC(&cfg, batch_sum_fn(family, a.redblack != 0, a.full != 0), args);
 }
 
-int batch_max_blocks_sum(int family, bool redblack) {
-    return device_sm_count() * blocks_per_sm(batch_sum_fn(family, redblack));
+int batch_max_blocks_sum(int family, bool redblack, bool full) {
+    return device_sm_count() * blocks_per_sm(batch_sum_fn(family, redblack, full));
 }
 
 }  // namespace bpg

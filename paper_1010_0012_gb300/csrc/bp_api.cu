@@ -22,7 +22,7 @@
 namespace bpg {
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
-int batch_max_blocks_sum(int family, bool redblack = false);
+int batch_max_blocks_sum(int family, bool redblack = false, bool full = false);
 int batch_max_blocks_min(int family, bool redblack = false, bool full = false);
 }  // namespace bpg
 

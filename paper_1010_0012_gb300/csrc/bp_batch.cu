@@ -24,7 +24,7 @@ using namespace bpg;
 namespace bpg {
 cudaError_t launch_batch_sum(const BatchArgs &a, int family, int blocks, cudaStream_t s);
 cudaError_t launch_batch_min(const BatchArgs &a, int family, int blocks, cudaStream_t s);
-int batch_max_blocks_sum(int family, bool redblack = false);
+int batch_max_blocks_sum(int family, bool redblack = false, bool full = false);
 int batch_max_blocks_min(int family, bool redblack = false, bool full = false);
 
 int batch_lanes_per_node(int family, int Mp) {
@@ -134,7 +134,7 @@ static bp_status build_items(bp_batch b) {
 
 static int batch_blocks(bp_batch b) {
     const int maxb = b->dtype == BP_I32 ? batch_max_blocks_min(b->family, false, b->all_full)
-                                        : batch_max_blocks_sum(b->family);
+                                        : batch_max_blocks_sum(b->family, false, b->all_full);
     return std::max(1, std::min(maxb, b->n_items));
 }
 

@@ -209,3 +209,10 @@ def test_batch_min_power_of_two_labels_bit_exact(family):
     mrfs = _mrfs(n=6, seed=11, label_counts=(16, 32, 64, 128, 256))
     res, _ = _run_batch(mrfs, H.bp().BP_I32, 6, family=family, tile=2048)
     _check_min(mrfs, res, 6)
+
+
+@pytest.mark.parametrize("family", [1, 2])
+def test_batch_sum_power_of_two_labels(family):
+    mrfs = _mrfs(n=6, seed=12, label_counts=(16, 32, 64, 128, 256))
+    res, _ = _run_batch(mrfs, H.bp().BP_F32, 6, family=family, tile=2048)
+    _check_sum(mrfs, res, 6)
