@@ -105,6 +105,31 @@ def test_band_written_as_lists_equals_the_band_kernel():
     np.testing.assert_array_equal(pl_s[side, rr, cc], pl_b[side, rr, cc])
 
 
+@pytest.mark.parametrize("dtype_name", ["f32", "i32"])
+def test_empty_pattern_leaves_only_the_constant_term(dtype_name):
+    """No compatible pair at all: every pair has fbar (Ebar), so every
+    message is uniform (1/M, or 0 for min-sum), whatever the inputs."""
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(5)
+    M, W, Hh = 24, 6, 5
+    rowptr = np.zeros(M + 1, np.int32)
+    if dtype_name == "f32":
+        g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
+        bel, mp, pl = _run(M, bp.BP_F32, None, g, (rowptr, np.zeros(0, np.int32), np.zeros(0, np.float32)),
+                           0.3, 2, "sync")
+        src, dst, side, rr, cc = grid.grid_edges(W, Hh)
+        np.testing.assert_allclose(pl[side, rr, cc][:, :M], 1.0 / M, rtol=1e-6)
+        b64 = g.astype(np.float64) / g.astype(np.float64).sum(-1, keepdims=True)
+        assert H.node_rel_err(bel, b64) <= H.REL_TOL
+    else:
+        E = rng.integers(0, 30, (Hh, W, M)).astype(np.int32)
+        bel, mp, pl = _run(M, bp.BP_I32, None, E, (rowptr, np.zeros(0, np.int32), np.zeros(0, np.int32)),
+                           7, 2, "sync")
+        src, dst, side, rr, cc = grid.grid_edges(W, Hh)
+        assert int(np.abs(pl[side, rr, cc][:, :M]).max()) == 0
+        np.testing.assert_array_equal(bel.astype(np.int64), E.astype(np.int64))
+
+
 def test_sparse_max_mode_rejects_energy_above_ebar():
     import torch
     from paper_1010_0012_gb300 import bp
