@@ -504,10 +504,12 @@ def run_dense_compare_workload(args):
 
 
 def l2_copy_probe(stream, mb=16, reps=200):
-    """Measured L2 bandwidth for workloads whose working set stays in L2: a
-    device-to-device copy between two `mb` MB buffers (both fit in L2 with
+    """A like-for-like bandwidth for workloads whose working set stays in L2:
+    a device-to-device copy between two `mb` MB buffers (both fit in L2 with
     room to spare), repeated `reps` times after a warm-up, timed with CUDA
-    events; read plus write bytes per second."""
+    events; read plus write bytes per second.  At 16 MB a copy moves 32 MB
+    per launch, what one red-black half-step of 384x288, M = 16 moves, so it
+    carries the same per-launch ramp and tail; it is not the L2 peak."""
     import torch
     n = mb * (1 << 20) // 4
     with torch.cuda.stream(stream):
@@ -524,7 +526,8 @@ def l2_copy_probe(stream, mb=16, reps=200):
     e1.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
     return {"copy_gbs": 2 * n * 4 / t / 1e9,
-            "how": f"copy between two {mb} MB device buffers, {reps} repetitions, CUDA events"}
+            "how": f"copy between two {mb} MB device buffers ({2 * mb} MB per launch), {reps} repetitions, "
+                   "CUDA events"}
 
 
 def run_grid_workload(args, name):
