@@ -297,13 +297,21 @@ def run_ours(args, cfg, rank, world):
     out = {"elapsed": elapsed, "units": units_all, "launches": launches, "layout": bp.bp_get_layout(G.h),
            "band_launch_s": band_s / (args.steps * K), "clocks": clk.summary()}
 
-    # end to end through the public API: every step uploads its unary from
-    # pinned host memory and reads its MAP back; the upload of step i+1 runs on
-    # a copy stream while step i computes (two device staging buffers)
-    if not args.no_e2e:
+    # end to end through the public API.  Every step uploads its inputs from
+    # pinned host memory and reads its MAP back; the upload of step i+1 runs
+    # on a copy stream while step i computes (two device staging buffers).
+    # "e2e": the inputs are the stereo pair (two 8-bit images) and the unary
+    # is formed on the device (bp_set_unary_stereo); "e2e_unary_upload": the
+    # precomputed FP32 unary [H][W][M] is uploaded instead (bp_set_unary).
+    def run_e2e(kind):
         n_e = max(1, args.steps)
         map_host = [torch.empty((cfg.H, cfg.W), dtype=torch.int32).pin_memory() for _ in range(2)]
-        bufs = [g_dev, torch.empty_like(g_dev)]
+        if kind == "stereo":
+            srcs = [torch.from_numpy(st.left).pin_memory(), torch.from_numpy(st.right).pin_memory()]
+            table = wl.unary_table_f32(cfg)
+        else:
+            srcs = [g_host]
+        bufs = [[torch.empty_like(t, device="cuda") for t in srcs] for _ in range(2)]
         copy_stream = torch.cuda.Stream()
         ready = [torch.cuda.Event() for _ in range(2)]
         consumed = [None, None]
@@ -316,13 +324,17 @@ def run_ours(args, cfg, rank, world):
             with torch.cuda.stream(copy_stream):
                 if consumed[b] is not None:
                     copy_stream.wait_event(consumed[b])
-                bufs[b].copy_(g_host, non_blocking=True)
+                for d, hsrc in zip(bufs[b], srcs):
+                    d.copy_(hsrc, non_blocking=True)
                 ready[b].record(copy_stream)
         upload(0)
         for i in range(n_e):
             b = i % 2
             stream.wait_event(ready[b])
-            G.set_unary(bufs[b])
+            if kind == "stereo":
+                G.set_unary_stereo(bufs[b][0], bufs[b][1], table, cfg.Tu)
+            else:
+                G.set_unary(bufs[b][0])
             consumed[b] = torch.cuda.Event()
             consumed[b].record(stream)
             if i + 1 < n_e:
@@ -335,9 +347,18 @@ def run_ours(args, cfg, rank, world):
         torch.cuda.synchronize()
         e_wall = time.perf_counter() - e0
         clk_e.__exit__()
-        out["e2e"] = {"value": units_step * n_e * world / e_wall, "unit": UNIT,
-                      "h2d_bytes_per_step": int(g_host.numel() * 4), "d2h_bytes_per_step": int(map_host[0].numel() * 4),
-                      "steps": n_e, "clocks": clk_e.summary()}
+        return {"value": units_step * n_e * world / e_wall, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in srcs)),
+                "d2h_bytes_per_step": int(map_host[0].numel() * 4), "steps": n_e,
+                "inputs": ("stereo pair [H][W] uint8 x 2, unary formed on the device" if kind == "stereo"
+                           else "unary [H][W][M] float32"),
+                "clocks": clk_e.summary()}
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e("stereo")
+        out["e2e_unary_upload"] = run_e2e("unary")
+        G.set_unary(g_dev)
+        torch.cuda.synchronize()
 
     # O(M^2) baselines on the same grid and state, timed per iteration
     if not args.no_baselines:
@@ -864,6 +885,7 @@ def main():
             "clocks": res["clocks"], "gpu_launches": res["launches"]}
     if "e2e" in res:
         line["e2e"] = res["e2e"]
+        line["e2e_unary_upload"] = res["e2e_unary_upload"]
     if "baselines" in res:
         line["baselines"] = res["baselines"]
     if not args.no_cpu_baseline:

@@ -41,6 +41,7 @@ def _load():
     sig = {
         "bp_create": ([I, I, I, I, P, ctypes.POINTER(P)], I),
         "bp_set_unary": ([P, P], I),
+        "bp_set_unary_stereo": ([P, P, P, P, I], I),
         "bp_set_unary_log": ([P, P], I),
         "bp_set_potential": ([P, P, I, D], I),
         "bp_set_potential_sparse": ([P, P, P, P, D], I),
@@ -142,6 +143,17 @@ def bp_destroy(h):
 
 def bp_set_unary(h, unary: torch.Tensor, dtype):
     _check(h, _lib.bp_set_unary(h, _dptr(unary, torch.float32 if dtype == BP_F32 else torch.int32)))
+
+
+def bp_set_unary_stereo(h, left: torch.Tensor, right: torch.Tensor, table, Tu: int, dtype):
+    """left, right: [H][W] uint8 device images; table: Tu + 1 values indexed
+    by the matching cost (float32 g or int32 E_u by the handle's dtype)."""
+    import numpy as np
+    arr = np.ascontiguousarray(table, dtype=np.float32 if dtype == BP_F32 else np.int32)
+    if arr.size != Tu + 1:
+        raise ValueError("table must hold Tu + 1 values")
+    _check(h, _lib.bp_set_unary_stereo(h, _dptr(left, torch.uint8), _dptr(right, torch.uint8),
+                                       arr.ctypes.data_as(ctypes.c_void_p), int(Tu)))
 
 
 def bp_set_unary_log(h, logg: torch.Tensor):
@@ -455,6 +467,11 @@ class BPGrid:
         if tuple(unary.shape) != (self.H, self.W, self.M):
             raise ValueError("unary must be [H][W][M]")
         bp_set_unary(self.h, unary, self.dtype)
+
+    def set_unary_stereo(self, left: torch.Tensor, right: torch.Tensor, table, Tu: int):
+        if tuple(left.shape) != (self.H, self.W) or tuple(right.shape) != (self.H, self.W):
+            raise ValueError("images must be [H][W]")
+        bp_set_unary_stereo(self.h, left, right, table, Tu, self.dtype)
 
     def set_potential(self, table, T, fbar):
         bp_set_potential(self.h, table, T, fbar, self.dtype)

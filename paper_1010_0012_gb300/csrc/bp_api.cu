@@ -410,6 +410,37 @@ bp_status bp_set_unary(bp_handle h, const void *dev_unary) {
     return BP_OK;
 }
 
+bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *dev_left, const uint8_t *dev_right,
+                              const void *host_table, int Tu) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary_stereo: NULL handle");
+    h->err.clear();
+    if (!dev_left || !dev_right || !host_table) return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: NULL argument");
+    if (Tu < 0 || Tu > kMaxStereoCost) return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: Tu must be in [0, 255]");
+    if (h->dtype == BP_F32) {
+        const float *t = (const float *)host_table;
+        for (int k = 0; k <= Tu; ++k)
+            if (!std::isfinite(t[k]) || t[k] < 0.f)
+                return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: table values must be finite and >= 0");
+    } else {
+        const int32_t *t = (const int32_t *)host_table;
+        for (int k = 0; k <= Tu; ++k)
+            if (t[k] < 0 || t[k] >= (1 << 26))
+                return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: energies must be in [0, 2^26)");
+    }
+    if (bp_status st = bpg_check_device(h)) return st;
+    if (h->dtype == BP_F32)
+        BP_CK(h, launch_unary_stereo_f32(dev_left, dev_right, (float *)h->unary, h->W, h->H, h->M, h->Mp, Tu,
+                                         (const float *)host_table, h->stream));
+    else
+        BP_CK(h, launch_unary_stereo_i32(dev_left, dev_right, (int32_t *)h->unary, h->W, h->H, h->M, h->Mp, Tu,
+                                         (const int32_t *)host_table, h->stream));
+    h->launches += 1;
+    h->have_unary = true;
+    h->log_unary_valid = false;
+    h->recorded = false;
+    return BP_OK;
+}
+
 bp_status bp_set_unary_log(bp_handle h, const float *dev_logg) {
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary_log: NULL handle");
     h->err.clear();

@@ -108,6 +108,14 @@ cudaError_t launch_band_min_generic(const BandArgsGenericI &a, cudaStream_t s);
 cudaError_t launch_dense_sum(const DenseArgsF &a, cudaStream_t s);
 cudaError_t launch_dense_min(const DenseArgsI &a, cudaStream_t s);
 
+// Stereo unary from the image pair (unary_stereo.cu): out[node][x] =
+// table[min(|R - L(c + x)|, Tu)] (Tu where c + x >= W), 0 on padded labels.
+constexpr int kMaxStereoCost = 255;
+cudaError_t launch_unary_stereo_f32(const uint8_t *left, const uint8_t *right, float *out, int W, int H, int M,
+                                    int Mp, int Tu, const float *host_table, cudaStream_t s);
+cudaError_t launch_unary_stereo_i32(const uint8_t *left, const uint8_t *right, int32_t *out, int W, int H, int M,
+                                    int Mp, int Tu, const int32_t *host_table, cudaStream_t s);
+
 // Utility kernels (aux_kernels.cu).
 // transform: 0 copy, 1 log, 2 exp
 cudaError_t launch_pad_copy_f32(const float *src, float *dst, long long nodes, int M, int Mp,

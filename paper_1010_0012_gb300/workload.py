@@ -163,15 +163,25 @@ def small_config(name: str, W: int, H: int, M: int, T: int, alpha: float = 1.0,
 # stereo model evaluated once in float64 and rounded once to the type the GPU
 # path stores (float32 or int32), so both sides see identical inputs.
 
+def unary_table_f32(cfg: GridConfig) -> np.ndarray:
+    """g as a function of the matching cost k = 0..Tu: exp(-beta * k) in
+    float64, rounded once to float32."""
+    return np.exp(-cfg.beta * np.arange(cfg.Tu + 1, dtype=np.float64)).astype(np.float32)
+
+
+def unary_table_i32(cfg: GridConfig) -> np.ndarray:
+    """E_u as a function of the matching cost k = 0..Tu: round(Q*beta) * k."""
+    return int(round(Q_ENERGY * cfg.beta)) * np.arange(cfg.Tu + 1, dtype=np.int32)
+
+
 def unary_f32(stereo: Stereo) -> np.ndarray:
     """g = exp(-beta * cost) as float32 [H][W][M] (FP64 exp, one rounding)."""
-    lut = np.exp(-stereo.cfg.beta * np.arange(stereo.cfg.Tu + 1, dtype=np.float64))
-    return lut.astype(np.float32)[stereo.cost]
+    return unary_table_f32(stereo.cfg)[stereo.cost]
 
 
 def unary_i32(stereo: Stereo) -> np.ndarray:
     """E_u = round(Q*beta) * cost as int32 [H][W][M]."""
-    return (int(round(Q_ENERGY * stereo.cfg.beta)) * stereo.cost.astype(np.int32))
+    return unary_table_i32(stereo.cfg)[stereo.cost]
 
 
 def pair_table_f32(alpha: float, T: int):
