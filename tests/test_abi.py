@@ -60,6 +60,50 @@ def test_argument_errors_without_gpu(lib):
     assert lib.bp_version() > 0
 
 
+HANDLE_TYPES = {"bp_handle": "bp_last_error", "bp_batch": "bp_batch_last_error",
+                "bp_factor_graph": "bp_fg_last_error"}
+
+
+def _ctype(param):
+    """ctypes type and a zero value for one C parameter declaration."""
+    decl = param.strip()
+    if "*" in decl or decl.split()[0] in HANDLE_TYPES:
+        return ctypes.c_void_p, None
+    kind = decl.rsplit(" ", 1)[0]
+    if "double" in kind:
+        return ctypes.c_double, 0.0
+    if "float" in kind:
+        return ctypes.c_float, 0.0
+    if "long long" in kind or "size_t" in kind:
+        return ctypes.c_longlong, 0
+    return ctypes.c_int, 0
+
+
+def test_every_handle_call_rejects_a_null_handle_without_a_gpu(lib):
+    """Every status-returning entry point that takes a handle first returns
+    BP_ERR_ARG for a NULL handle, before any other argument or the device is
+    touched, and records a message naming itself where the header says
+    (bp_last_error / bp_batch_last_error / bp_fg_last_error of NULL)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = re.findall(r"\bbp_status\s+(bp_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text)
+    checked = 0
+    for name, params in decls:
+        ps = [p for p in params.split(",") if p.strip()]
+        if not ps or ps[0].split()[0] not in HANDLE_TYPES:
+            continue
+        err = getattr(lib, HANDLE_TYPES[ps[0].split()[0]])
+        err.restype = ctypes.c_char_p
+        err.argtypes = [ctypes.c_void_p]
+        types, vals = zip(*[_ctype(p) for p in ps])
+        fn = getattr(lib, name)
+        fn.argtypes = list(types)
+        fn.restype = ctypes.c_int
+        assert fn(*vals) == 1, name
+        assert name.encode() in err(None), (name, err(None))
+        checked += 1
+    assert checked >= 35
+
+
 def test_binding_names_match_the_abi():
     """The Python binding exposes one function per C entry point, same name."""
     import ast
