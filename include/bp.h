@@ -85,15 +85,18 @@ bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_h
 bp_status bp_set_unary(bp_handle h, const void *dev_unary);
 
 /* The unary of the stereo model (Sec. 6) formed on the device from the image
- * pair: dev_left, dev_right [H][W] uint8 (row-major device images, right =
- * reference), cost(r, c, x) = min(|R(r,c) - L(r,c+x)|, Tu), and Tu where
- * c + x >= W.  host_table holds Tu + 1 values indexed by the cost: float32 g
- * (e.g. exp(-beta cost)) for BP_F32, int32 energies E_u for BP_I32; it is
- * read during the call (no copy of it outlives the call), the images are
- * read on the handle's stream and must stay valid until that work has run.
- * Equivalent to bp_set_unary of table[cost].  BP_ERR_ARG for Tu outside
- * [0, 255], a negative or non-finite g, or an energy outside [0, 2^26). */
-bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *dev_left, const uint8_t *dev_right,
+ * pair: left, right [H][W] uint8 (row-major, right = reference),
+ * cost(r, c, x) = min(|R(r,c) - L(r,c+x)|, Tu), and Tu where c + x >= W.
+ * host_table holds Tu + 1 values indexed by the cost: float32 g (e.g.
+ * exp(-beta cost)) for BP_F32, int32 energies E_u for BP_I32; it is read
+ * during the call.  The images may be device (or managed) memory, read in
+ * place on the handle's stream, or host memory, which the call copies into a
+ * handle-owned staging buffer on that stream (asynchronously from pinned
+ * memory, before returning from pageable memory); either way they must stay
+ * valid until that work has run.  Equivalent to bp_set_unary of
+ * table[cost].  BP_ERR_ARG for Tu outside [0, 255], a negative or non-finite
+ * g, or an energy outside [0, 2^26). */
+bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *left, const uint8_t *right,
                               const void *host_table, int Tu);
 
 /* The same unary given as log g (BP_F32 only): dev_logg [H][W][M] float32.

@@ -145,14 +145,25 @@ def bp_set_unary(h, unary: torch.Tensor, dtype):
     _check(h, _lib.bp_set_unary(h, _dptr(unary, torch.float32 if dtype == BP_F32 else torch.int32)))
 
 
+def _image_ptr(t: torch.Tensor):
+    """A [H][W] uint8 image on the device or in host memory (the library
+    copies host images itself)."""
+    if t.is_cuda:
+        return _dptr(t, torch.uint8)
+    if t.dtype != torch.uint8 or not t.is_contiguous():
+        raise TypeError("expected a contiguous uint8 image")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def bp_set_unary_stereo(h, left: torch.Tensor, right: torch.Tensor, table, Tu: int, dtype):
-    """left, right: [H][W] uint8 device images; table: Tu + 1 values indexed
-    by the matching cost (float32 g or int32 E_u by the handle's dtype)."""
+    """left, right: [H][W] uint8 images, on the device or in (preferably
+    pinned) host memory; table: Tu + 1 values indexed by the matching cost
+    (float32 g or int32 E_u by the handle's dtype)."""
     import numpy as np
     arr = np.ascontiguousarray(table, dtype=np.float32 if dtype == BP_F32 else np.int32)
     if arr.size != Tu + 1:
         raise ValueError("table must hold Tu + 1 values")
-    _check(h, _lib.bp_set_unary_stereo(h, _dptr(left, torch.uint8), _dptr(right, torch.uint8),
+    _check(h, _lib.bp_set_unary_stereo(h, _image_ptr(left), _image_ptr(right),
                                        arr.ctypes.data_as(ctypes.c_void_p), int(Tu)))
 
 

@@ -386,7 +386,7 @@ void bp_destroy(bp_handle h) {
     clear_graphs(h);
     bpg_free_extras(h);
     void *bufs[] = {h->unary, h->log_unary, h->msg[0], h->msg[1], h->d_wf, h->d_wi, h->d_dense, h->d_status,
-                    h->tune_buf, h->d_sp_len, h->d_sp_ell};
+                    h->tune_buf, h->d_sp_len, h->d_sp_ell, h->d_stereo};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -410,11 +410,11 @@ bp_status bp_set_unary(bp_handle h, const void *dev_unary) {
     return BP_OK;
 }
 
-bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *dev_left, const uint8_t *dev_right,
+bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *left, const uint8_t *right,
                               const void *host_table, int Tu) {
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary_stereo: NULL handle");
     h->err.clear();
-    if (!dev_left || !dev_right || !host_table) return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: NULL argument");
+    if (!left || !right || !host_table) return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: NULL argument");
     if (Tu < 0 || Tu > kMaxStereoCost) return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: Tu must be in [0, 255]");
     if (h->dtype == BP_F32) {
         const float *t = (const float *)host_table;
@@ -428,11 +428,24 @@ bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *dev_left, const uint8_
                 return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: energies must be in [0, 2^26)");
     }
     if (bp_status st = bpg_check_device(h)) return st;
+    // images in host memory (pinned or pageable) are copied into the handle's
+    // staging buffer on its stream first; device or managed memory is read
+    // in place
+    const uint8_t *img[2] = {left, right};
+    const size_t img_bytes = (size_t)h->W * h->H;
+    for (int k = 0; k < 2; ++k) {
+        cudaPointerAttributes at{};
+        BP_CK(h, cudaPointerGetAttributes(&at, img[k]));
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) continue;
+        if (bp_status st = ensure_buffer(h, (void **)&h->d_stereo, 2 * img_bytes, "stereo image staging")) return st;
+        BP_CK(h, cudaMemcpyAsync(h->d_stereo + k * img_bytes, img[k], img_bytes, cudaMemcpyHostToDevice, h->stream));
+        img[k] = h->d_stereo + k * img_bytes;
+    }
     if (h->dtype == BP_F32)
-        BP_CK(h, launch_unary_stereo_f32(dev_left, dev_right, (float *)h->unary, h->W, h->H, h->M, h->Mp, Tu,
+        BP_CK(h, launch_unary_stereo_f32(img[0], img[1], (float *)h->unary, h->W, h->H, h->M, h->Mp, Tu,
                                          (const float *)host_table, h->stream));
     else
-        BP_CK(h, launch_unary_stereo_i32(dev_left, dev_right, (int32_t *)h->unary, h->W, h->H, h->M, h->Mp, Tu,
+        BP_CK(h, launch_unary_stereo_i32(img[0], img[1], (int32_t *)h->unary, h->W, h->H, h->M, h->Mp, Tu,
                                          (const int32_t *)host_table, h->stream));
     h->launches += 1;
     h->have_unary = true;

@@ -59,6 +59,7 @@ struct bp_ctx {
     std::vector<float> sp_valf;      // f(x_i, x_j)
     std::vector<int32_t> sp_vali;    // E(x_i, x_j)
     void *d_sp_len = nullptr, *d_sp_ell = nullptr;   // device pattern (see bp_sparse.h)
+    uint8_t *d_stereo = nullptr;     // staging of host images for bp_set_unary_stereo (2 W H bytes)
 
     bpg::Layout layout{32, 1};
     bpg::Layout log_layout{32, 1};  // layout of the log-domain forward and adjoint kernels

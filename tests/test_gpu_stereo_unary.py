@@ -139,3 +139,38 @@ def test_stereo_unary_at_the_benchmark_size():
     assert bool(torch.equal(ba, bb)) and bool(torch.equal(ma, mb))
     A.close()
     B.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_stereo_unary_from_host_images(pinned):
+    """Host images (pinned or pageable) are copied by the library itself and
+    give the device images' unary bit for bit, also when the host buffers are
+    overwritten right after the call returns (the next call's images)."""
+    import torch
+    from paper_1010_0012_gb300 import bp
+    cfg = wl.small_config("sh", 37, 11, 24, 2, seed=91, noise_sigma=3.0)
+    st, L, R = _pair(cfg)
+    other = wl.make_stereo(wl.small_config("sh2", 37, 11, 24, 2, seed=92, noise_sigma=3.0))
+    table = wl.unary_table_f32(cfg)
+    hl, hr = torch.from_numpy(st.left.copy()), torch.from_numpy(st.right.copy())
+    if pinned:
+        hl, hr = hl.pin_memory(), hr.pin_memory()
+    tab, fb = wl.pair_table_f32(cfg.alpha, cfg.T)
+    out = []
+    for source in ("device", "host"):
+        G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_F32)
+        G.set_potential(tab, cfg.T, fb)
+        if source == "device":
+            G.set_unary_stereo(L, R, table, cfg.Tu)
+        else:
+            G.set_unary_stereo(hl, hr, table, cfg.Tu)
+            G.sync()                       # the copies have run; reuse the host buffers
+            hl.copy_(torch.from_numpy(other.left))
+            hr.copy_(torch.from_numpy(other.right))
+        G.reset()
+        G.iterate(2, bp.BP_SUM, "sync")
+        bel, mp = G.beliefs()
+        G.sync()
+        out.append((bel.cpu().numpy(), mp.cpu().numpy()))
+        G.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
