@@ -74,7 +74,8 @@ typedef enum {
                             /* update; M 33..128)                                     */
 } bp_dense_kind;
 
-/* Create a handle for an H x W grid with M labels (2 <= M <= 1024,
+/* Create a handle for the pairwise MRF of Eq. 1 on an H x W 4-connected grid
+ * (the stereo lattice of Sec. 6) with M labels (2 <= M <= 1024,
  * 1 <= W, H, W*H*M < 2^31).  cuda_stream: a cudaStream_t to order all work on,
  * or NULL for a stream the handle creates (blocking with respect to the legacy
  * default stream).  Allocates the message buffers.  On error *out is NULL. */
@@ -99,8 +100,9 @@ bp_status bp_set_unary(bp_handle h, const void *dev_unary);
 bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *left, const uint8_t *right,
                               const void *host_table, int Tu);
 
-/* The same unary given as log g (BP_F32 only): dev_logg [H][W][M] float32.
- * Log-domain runs use these values as they are (no round trip through g). */
+/* The same unary (Eq. 1's g) given as log g (BP_F32 only): dev_logg
+ * [H][W][M] float32.  Log-domain runs use these values as they are (no round
+ * trip through g); it is the parameter bp_backward differentiates against. */
 bp_status bp_set_unary_log(bp_handle h, const float *dev_logg);
 
 /* Pairwise potential with the sparse compatibility property (Sec. 4):
@@ -127,11 +129,15 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
 bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
                                   const void *host_vals, double fbar);
 
-/* Uniform initial messages: 1/M (sum), 0 (min-sum), log(1/M) (log mode). */
+/* Uniform initial messages: 1/M (sum), 0 (min-sum), log(1/M) (log mode).
+ * The paper leaves the start state open (Sec. 2 runs BP from any messages);
+ * uniform is the usual choice and is normalised as after Eq. 2. */
 bp_status bp_reset_messages(bp_handle h);
 
-/* Run n_iters iterations of the O(mM) update under `schedule`.
- * mode: BP_SUM (needs BP_F32), BP_MAX (needs BP_I32), or BP_SUM|BP_LOG and
+/* Run n_iters iterations of the O(mM) update under `schedule`: Eq. 7 for
+ * sum-product, Eq. 11 (energies) for max-product, every message of every
+ * node per iteration (Sec. 4's per-message cost O(mM) instead of Eq. 2's
+ * O(M^2)).  mode: BP_SUM (needs BP_F32), BP_MAX (needs BP_I32), or BP_SUM|BP_LOG and
  * BP_SUM|BP_LOG|BP_RECORD (log-messages, BP_SYNC only).  Messages are
  * normalised after each update (sum 1, or minimum 0 for min-sum). */
 bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule);
@@ -159,8 +165,8 @@ bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind);
  * receives the MAP label: argmax (sum) / argmin (min-sum), lowest label on ties. */
 bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map);
 
-/* Copy the current message planes out / in ([4][H][W][M], dtype of the
- * handle).  Float32 messages cross this boundary linear (normalised) in every
+/* Copy the current message planes out / in: the messages m_ij(x_j) of Eq. 2
+ * ([4][H][W][M], dtype of the handle).  Float32 messages cross this boundary linear (normalised) in every
  * mode: after log-mode iterations bp_get_messages returns exp of the
  * log-domain state, and bp_set_messages installs a linear state.  Used to
  * checkpoint or inject a state. */
@@ -168,7 +174,12 @@ bp_status bp_get_messages(bp_handle h, void *dev_planes);
 bp_status bp_set_messages(bp_handle h, const void *dev_planes);
 
 /* Reverse mode of the recorded log-domain sum-product run (bp_iterate with
- * BP_SUM|BP_LOG|BP_RECORD) followed by bp_beliefs.  Given
+ * BP_SUM|BP_LOG|BP_RECORD) followed by bp_beliefs: the gradient of a loss of
+ * the beliefs (Eq. 3) through the unrolled Eq. 7 updates, for learning the
+ * potentials (parameter estimation needs sum-product marginals, Sec. 2 and
+ * Sec. 7).  The
+ * adjoint of Eq. 7 is again a band of width 2T + 1 plus a constant term, so
+ * it also costs O(mM) per message.  Given
  * dev_dlogb = dL/d log b [H][W][M], writes dev_dlogg = dL/d log g [H][W][M]
  * and, in float64, host_dtable[d + T] = dL/d f(d) (2T + 1 values) and
  * *host_dfbar = dL/d fbar, with f(d) and fbar independent parameters.
@@ -176,21 +187,27 @@ bp_status bp_set_messages(bp_handle h, const void *dev_planes);
 bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
                       double *host_dfbar);
 
-/* Checkpoint interval used by BP_RECORD runs (default 5). */
+/* Checkpoint interval used by BP_RECORD runs (default 5): the recorded run
+ * keeps every `every`-th message state, and bp_backward recomputes the states
+ * between them (no counterpart in the paper). */
 bp_status bp_set_checkpoint_interval(bp_handle h, int every);
 
-/* Wait for the handle's stream; reports device errors and time-outs. */
+/* Wait for the handle's stream; reports device errors and time-outs (no
+ * counterpart in the paper, like the rest of the handle management). */
 bp_status bp_sync(bp_handle h);
 
-/* Last error message of the handle (never NULL; "" if none).  Valid until
+/* Last error message of the handle (never NULL; "" if none; no counterpart
+ * in the paper).  Valid until
  * the next call on the handle.  bp_last_error(NULL) reports errors of
  * bp_create and of calls given a NULL handle. */
 const char *bp_last_error(bp_handle h);
 
-/* Release everything the handle owns.  NULL is ignored. */
+/* Release everything the handle owns.  NULL is ignored (no counterpart in
+ * the paper). */
 void bp_destroy(bp_handle h);
 
-/* ---- tuning ---------------------------------------------------------------
+/* ---- tuning (no counterpart in the paper: how the O(mM) update of Eq. 7 /
+ * Eq. 11 maps onto the GPU; results do not depend on these settings) ---------
  * The O(mM) kernel assigns L lanes to a node, each lane holding V = 4C
  * consecutive labels (L * 4C = padded label count).  The log-domain kernels
  * (BP_LOG iterations, the recorded forward and its adjoint) keep a layout of
@@ -202,7 +219,8 @@ bp_status bp_set_layout(bp_handle h, int lanes_per_node, int vec_chunks);
 bp_status bp_get_layout(bp_handle h, int *lanes_per_node, int *vec_chunks);
 bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms);
 /* Blocks per launch of the O(mM) register kernels (grid-stride over nodes);
- * 0 (default) = SM count x resident blocks per SM. */
+ * 0 (default) = SM count x resident blocks per SM.  Tuning, as above: no
+ * counterpart in the paper. */
 bp_status bp_set_grid(bp_handle h, int blocks);
 
 /* Allocation-free dense tensor-core iteration (no counterpart in the paper;
@@ -256,32 +274,40 @@ typedef struct bp_batch_ctx *bp_batch;
  * E(d) > Ebar), allocate every MRF's unary and two message states, copy the
  * unaries, and cut the nodes into work items.  cuda_stream as in bp_create. */
 bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void *cuda_stream, bp_batch *out);
+/* Uniform start state of every MRF (as bp_reset_messages). */
 bp_status bp_batch_reset_messages(bp_batch b);
-/* n_iters synchronous iterations of every MRF in one launch.  mode BP_SUM
+/* n_iters synchronous iterations (Eq. 7 or Eq. 11, each MRF with its own
+ * potential) of every MRF in one launch.  mode BP_SUM
  * (float32 batch) or BP_MAX (int32 batch).  Between iterations the blocks meet
  * at a grid barrier whose wait is bounded; a wait that runs out ends the
  * kernel and the next bp_batch_sync returns BP_ERR_TIMEOUT. */
 bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode);
-/* Beliefs / MAP (as bp_beliefs) and message planes (as bp_get_messages) of MRF k. */
+/* Beliefs / MAP (Eq. 3, as bp_beliefs) and message planes (as
+ * bp_get_messages) of MRF k; BP_ERR_ARG for k outside [0, n). */
 bp_status bp_batch_beliefs(bp_batch b, int k, void *dev_out, int32_t *dev_map);
 bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes);
-/* Work decomposition: family 1 (4 labels per lane, C = 1) or 2 (8 labels per
- * lane) and the item size in label words.  bp_batch_autotune times every
+/* Work decomposition (no counterpart in the paper; results do not depend on
+ * it): family 1 (4 labels per lane, C = 1) or 2 (8 labels per lane) and the
+ * item size in label words.  bp_batch_autotune times every
  * candidate on this batch, keeps the fastest (cached in $BP_AUTOTUNE_CACHE when
  * set) and resets the messages. */
 bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words);
 bp_status bp_batch_get_tiling(bp_batch b, int *family, int *tile_words);
 bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms);
-/* Bound of the grid-barrier wait (default 2 s).  extra_arrivals = 1 makes the
+/* Bound of the grid-barrier wait (default 2 s; failure detection, no
+ * counterpart in the paper).  extra_arrivals = 1 makes the
  * barrier wait for one block that does not exist, so that every wait runs
  * out: a fault-free way to exercise the time-out path. */
 bp_status bp_batch_set_wait_limit(bp_batch b, double seconds, int extra_arrivals);
+/* As bp_sync, bp_last_error (NULL: errors of bp_batch_create and of calls
+ * given a NULL batch), bp_launch_count and bp_destroy, for a batch. */
 bp_status bp_batch_sync(bp_batch b);
 const char *bp_batch_last_error(bp_batch b);
 long long bp_batch_launch_count(bp_batch b);
 void bp_batch_destroy(bp_batch b);
 
-/* How bp_iterate issues the linear sum-product and min-sum updates:
+/* How bp_iterate issues the linear sum-product and min-sum updates (no
+ * counterpart in the paper; the updates themselves are Eq. 7 / Eq. 11):
  * 0: one launch per iteration (two per red-black iteration);
  * 1: ONE persistent cooperative launch for the whole call, with a bounded grid
  *    barrier between iterations (half-steps), where served (16 < Mp <= 256
@@ -305,36 +331,48 @@ bp_status bp_set_persistent(bp_handle h, int mode);
  * 2 <= M <= 256; a variable may belong to at most 16 factors. */
 typedef struct bp_fg_ctx *bp_factor_graph;
 
+/* A factor graph of n_vars variables and n_factors three-variable factors
+ * (Sec. 7); cuda_stream and errors as in bp_create. */
 bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_factor_vars, bp_dtype dtype,
                        void *cuda_stream, bp_factor_graph *out);
-/* dev_unary [n_vars][M]: float32 g > 0 or int32 energies; copied. */
+/* Unaries g_v (Eq. 1's single-variable factors), dev_unary [n_vars][M]:
+ * float32 g > 0 or int32 energies; copied. */
 bp_status bp_fg_set_unary(bp_factor_graph g, const void *dev_unary);
-/* host_triplets [C][3] distinct (x_0, x_1, x_2) in [0, M); host_vals [C] f
+/* The shared factor potential with sparse compatibility (Sec. 7: C listed
+ * triplets, fbar elsewhere).  host_triplets [C][3] distinct (x_0, x_1, x_2)
+ * in [0, M); host_vals [C] f
  * (float32) or E (int32); fbar (or the integer Ebar) elsewhere.
  * BP_ERR_POTENTIAL in max mode if some E > Ebar.  The table is copied to the
  * device as three per-slot lists (8 bytes per output label per entry of the
  * longest list of that slot). */
 bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplets, const void *host_vals,
                            double fbar);
+/* Uniform start state (as bp_reset_messages). */
 bp_status bp_fg_reset_messages(bp_factor_graph g);
-/* n_iters flooding iterations, mode BP_SUM (float32) or BP_MAX (int32). */
+/* n_iters flooding iterations, mode BP_SUM (float32) or BP_MAX (int32), with
+ * the O(C + M) factor update above (Sec. 7's extension of Eq. 7 / Eq. 11). */
 bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode);
-/* The same iterations with the standard O(M^3) factor update, for comparison. */
+/* The same iterations with the standard O(M^3) factor update (the sum over
+ * all M^2 pairs of the other two variables, the cost Sec. 7 avoids), for
+ * comparison. */
 bp_status bp_fg_iterate_dense(bp_factor_graph g, int n_iters, int mode);
-/* Beliefs [n_vars][M] (normalised float32, or int32 E_v + sum of messages) and
- * MAP labels (nullable), lowest label on ties. */
+/* Beliefs (Eq. 3 on the factor graph) [n_vars][M] (normalised float32, or
+ * int32 E_v + sum of messages) and MAP labels (nullable), lowest label on ties. */
 bp_status bp_fg_beliefs(bp_factor_graph g, void *dev_out, int32_t *dev_map);
-/* Factor-to-variable messages [n_factors][3][M] (slot order). */
+/* Factor-to-variable messages m_{a->v} (Sec. 7) [n_factors][3][M] (slot order). */
 bp_status bp_fg_get_messages(bp_factor_graph g, void *dev_out);
+/* As bp_sync, bp_last_error (NULL: errors of bp_fg_create and of calls given
+ * a NULL graph), bp_launch_count and bp_destroy, for a factor graph. */
 bp_status bp_fg_sync(bp_factor_graph g);
 const char *bp_fg_last_error(bp_factor_graph g);
 long long bp_fg_launch_count(bp_factor_graph g);
 void bp_fg_destroy(bp_factor_graph g);
 
-/* Number of kernel launches the library issued on this handle so far. */
+/* Number of kernel launches the library issued on this handle so far (no
+ * counterpart in the paper; lets a caller count the GPU work of a call). */
 long long bp_launch_count(bp_handle h);
 
-/* Library version, (major << 16) | minor. */
+/* Library version, (major << 16) | minor (no counterpart in the paper). */
 int bp_version(void);
 
 #ifdef __cplusplus
