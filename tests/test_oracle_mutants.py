@@ -26,6 +26,8 @@ MUTANTS = {
     # colour 1 half-step first
     "colour_order": ("for (int c = 0; c < 2 && rc == 0; ++c) {",
                      "for (int c = 1; c >= 0 && rc == 0; --c) {"),
+    # f(x_j, x_i) instead of f(x_i, x_j): invisible with symmetric tables
+    "transposed_table": ("u += F[(size_t)xi * M + xj] * h[xi];", "u += F[(size_t)xj * M + xi] * h[xi];"),
 }
 
 
@@ -50,6 +52,8 @@ def _run_with(lib, fn, *args, **kw):
         getattr(lib, nm).argtypes = [I, I, I, P, P, P, P, P, I, I, P]
     for nm in ("oracle_sum_beliefs", "oracle_min_beliefs"):
         getattr(lib, nm).argtypes = [I, I, I, P, P, P, P]
+    for nm in ("oracle_sum_edge_update", "oracle_min_edge_update"):
+        getattr(lib, nm).argtypes = [I, P, I, P, P, P]
     try:
         return fn(*args, **kw)
     finally:
@@ -118,3 +122,27 @@ def test_schedule_mutant_is_caught():
     lib = _build_mutant("colour_order")
     assert not _sum_pin_passes(lib, schedule="redblack", chain=True)
     assert _sum_pin_passes(oracle._load(), schedule="redblack", chain=True)
+
+
+def _eq7_pin_passes(lib):
+    """The Eq. 7 pin (tests/test_oracle_algebra.py) on asymmetric band tables."""
+    from oracle import stereo
+    from tests.test_oracle_algebra import eq7
+    ok = True
+    for M, T in ((5, 1), (16, 2)):
+        rng = np.random.default_rng(M + T)
+        g = rng.uniform(0.05, 1.0, M)
+        incoming = [rng.uniform(0.05, 1.0, M) for _ in range(3)]
+        fbar = 0.1
+        band = rng.uniform(0.2, 2.0, 2 * T + 1)
+        F = stereo.compatibility_matrix(band, T, fbar, M)
+        ref = _run_with(lib, oracle.sum_edge_update, g, incoming, F)
+        ok &= np.allclose(eq7(g, incoming, band, T, fbar, M), ref, rtol=1e-12, atol=0)
+    return ok
+
+
+def test_transposed_table_mutant_is_caught_by_the_eq7_pin():
+    lib = _build_mutant("transposed_table")
+    assert _sum_pin_passes(lib)              # the tree pins use symmetric tables: blind to it
+    assert not _eq7_pin_passes(lib)
+    assert _eq7_pin_passes(oracle._load())
