@@ -245,3 +245,34 @@ def test_sparse_lists_of_a_band_give_the_band_matrix():
         rowptr.append(len(cols))
     np.testing.assert_array_equal(stereo.sparse_compatibility_matrix(rowptr, cols, vals, 0.05, M),
                                   stereo.compatibility_matrix(band, T, 0.05, M))
+
+
+@pytest.mark.parametrize("M", [2, 3, 7])
+def test_two_node_mrf_closed_form(M):
+    """Two nodes joined by one edge with an asymmetric table: after one
+    iteration the message 0 -> 1 is sum_{x_0} f(x_0, x_1) g_0(x_0) (Eq. 2
+    with no other incoming message), normalised, and the message 1 -> 0 is
+    sum_{x_1} f(x_1, x_0) g_1(x_1): the table is indexed (sender, receiver).
+    Node 1's belief is then its exact marginal g_1(x_1) sum_{x_0} g_0 f /Z,
+    and min-sum gives the exact min-marginal E_1(x_1) + min_{x_0} [E_0 + V]."""
+    rng = np.random.default_rng(M)
+    src, dst = np.array([0, 1]), np.array([1, 0])
+    g = rng.uniform(0.05, 1.0, (2, M))
+    F = rng.uniform(0.1, 2.0, (M, M))                 # F[x_sender, x_receiver]
+    msg = oracle.sum_product(src, dst, g, F, 1)
+    m01 = g[0] @ F
+    m10 = g[1] @ F
+    np.testing.assert_allclose(msg[0], m01 / m01.sum(), rtol=1e-13)
+    np.testing.assert_allclose(msg[1], m10 / m10.sum(), rtol=1e-13)
+    bel = oracle.sum_beliefs(dst, g, msg)
+    joint = g[0][:, None] * g[1][None, :] * F        # P(x_0, x_1) with the edge's f(x_0, x_1)
+    np.testing.assert_allclose(bel[1], joint.sum(0) / joint.sum(), rtol=1e-12)
+
+    Eu = rng.integers(0, 30, (2, M))
+    V = rng.integers(0, 20, (M, M))                   # V[x_sender, x_receiver]
+    msg = oracle.min_sum(src, dst, Eu, V, 1)
+    u01 = np.min(Eu[0][:, None] + V, axis=0)
+    np.testing.assert_array_equal(msg[0], u01 - u01.min())
+    bel = oracle.min_beliefs(dst, Eu, msg)
+    ref = Eu[1] + np.min(Eu[0][:, None] + V, axis=0)
+    np.testing.assert_array_equal(bel[1] - bel[1].min(), ref - ref.min())
