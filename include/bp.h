@@ -15,7 +15,12 @@
  *  - Arrays passed as `dev_*` are CUDA device pointers on the current device;
  *    arrays passed as `host_*` are host pointers.  The library never keeps a
  *    caller pointer after a call returns: inputs are copied into buffers the
- *    handle owns, outputs are written into caller buffers.
+ *    handle owns, outputs are written into caller buffers.  Device inputs are
+ *    read, and outputs written, by work on the handle's stream that may still
+ *    be running when the call returns: keep such a buffer unchanged (and
+ *    allocated) until that stream has reached the work, e.g. by bp_sync or by
+ *    ordering the caller's stream after it.  Host arrays are read before the
+ *    call returns, except where a call says otherwise.
  *  - Layouts are C order with the label innermost: a unary or belief array is
  *    [H][W][M]; message planes are [4][H][W][M], where plane s holds the
  *    message INTO node (r, c) from its neighbour on side s
