@@ -59,3 +59,57 @@ def test_dense_table_is_constant_outside_the_triplets():
     F = factor.dense_table([(0, 1, 2), (2, 2, 2)], [5.0, 7.0], 0.5, 3)
     assert F[0, 1, 2] == 5.0 and F[2, 2, 2] == 7.0
     assert np.count_nonzero(F != 0.5) == 2
+
+
+# Plausible mistakes planted in a private copy of the factor-graph oracle; the
+# brute-force tree pins above must fail for each.
+FACTOR_MUTANTS = {
+    # the variable-to-factor message keeps the factor's own message (Sec. 7's
+    # flooding update leaves it out)
+    "no_exclusion": ("if (b, t) != (a, s):", "if True:"),
+    # slot 1's sum contracts the other two slots' messages against the wrong axes
+    "swapped_slots": ('np.einsum("abc,a,c->b", F, n[0], n[2])', 'np.einsum("abc,c,a->b", F, n[0], n[2])'),
+    # min-sum slot 2 broadcasts slot 1's message along the wrong axis
+    "min_broadcast": ("V + n[0][:, None, None] + n[1][None, :, None], axis=(0, 1)",
+                      "V + n[0][:, None, None] + n[1][:, None, None], axis=(0, 1)"),
+    # beliefs without the unary
+    "no_unary_belief": ("bel = g.copy()", "bel = np.ones_like(g)"),
+}
+
+
+def _mutant_module(name):
+    import types
+    old, new = FACTOR_MUTANTS[name]
+    src = open(factor.__file__).read()
+    assert old in src, name
+    mod = types.ModuleType(f"factor_{name}")
+    exec(compile(src.replace(old, new, 1), f"<factor mutant {name}>", "exec"), mod.__dict__)
+    return mod
+
+
+def _tree_pins_pass(mod):
+    ok = True
+    for factors in TREES:
+        rng = np.random.default_rng(len(factors))
+        nv = 1 + max(max(f) for f in factors)
+        M = 3
+        g = rng.uniform(0.05, 1.0, (nv, M))
+        trip = [(a, b, c) for a in range(M) for b in range(M) for c in range(M) if rng.random() < 0.3]
+        F = mod.dense_table(trip, rng.uniform(0.5, 2.0, len(trip)), 0.2, M)
+        _, bel = mod.sum_product(g, factors, F, n_iters=2 * len(factors) + 2)
+        ok &= np.allclose(bel, _brute(g, factors, F, "sum"), rtol=1e-11)
+        E = rng.integers(0, 15, (nv, M))
+        V = mod.dense_table(trip, rng.integers(0, 8, len(trip)), 9, M, dtype=np.int64)
+        _, belm = mod.min_sum(E, factors, V, n_iters=2 * len(factors) + 2)
+        ref = _brute(E, factors, V, "min")
+        ok &= np.array_equal(belm - belm.min(1, keepdims=True), ref - ref.min(1, keepdims=True))
+    return ok
+
+
+def test_unmutated_factor_oracle_passes_the_tree_pins():
+    assert _tree_pins_pass(factor)
+
+
+@pytest.mark.parametrize("name", sorted(FACTOR_MUTANTS))
+def test_factor_mutant_is_caught(name):
+    assert not _tree_pins_pass(_mutant_module(name))
