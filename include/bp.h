@@ -243,15 +243,25 @@ bp_status bp_set_grid(bp_handle h, int blocks);
  *                   M = 128, <= 65536 at M = 64); larger sizes return BP_ERR_ARG.
  *   dev_unary       [H][W][M] float32 g > 0;
  *   dev_in_planes   [4][H][W][M] float32 current messages (layout as above);
- *   dev_out_planes  [4][H][W][M] float32 updated messages (must differ from
- *                   dev_in_planes); slots without a neighbour receive 0;
- *   host_table      2T+1 float32 values f(d), d = -T..T, and fbar outside.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  The call enqueues its kernels on cuda_stream (NULL: the legacy
- * default stream) and returns after they have completed.  All calls share the
- * one array, which keeps the last call's contents: calls that overlap on the
- * GPU (other streams, other host threads) race and must be serialised by the
+ *   dev_out_planes  [4][H][W][M] float32 updated messages, a range that must
+ *                   not overlap dev_in_planes; slots without a neighbour
+ *                   receive 0;
+ *   host_table      2T+1 float32 values f(d), d = -T..T, and fbar outside
+ *                   (for T >= M only d = -(M-1)..M-1 is read).
+ * The three device pointers must be 16-byte aligned (the kernels move 16-byte
+ * vectors); a misaligned or overlapping argument returns BP_ERR_ARG before
+ * anything is launched.
+ * Set-up: the first call on a device (and again after the device's context
+ * changes, e.g. after cudaDeviceReset) looks up the array's device address
+ * with that device current.  Under lazy module loading that first call is also
+ * the one that loads the library's kernels, at which point the driver places
+ * the 32 MiB array on the device: make it once at start-up, as a warm-up.
+ * The call enqueues its kernels on cuda_stream (NULL: the legacy default
+ * stream), then synchronises that stream and reads a status word back, so it
+ * returns after its kernels have completed and cannot be captured into a CUDA
+ * graph (a capturing stream returns BP_ERR_STATE).  All calls share the one
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
  * caller.  Errors are reported through bp_last_error(NULL). */
 bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const float *dev_unary, const float *dev_in_planes,
                                       float *dev_out_planes, const float *host_table, int T, double fbar,

@@ -13,7 +13,8 @@ constexpr int kGenBlock = 256;
 constexpr int kGenWarps = kGenBlock / 32;
 constexpr int32_t kBig = 1 << 30;
 
-int g_sm_count = 0;
+// SM count per device ordinal (a process may drive several devices)
+int g_sm_count[kMaxDevices] = {};
 
 // Sum (or min) of four per-thread values over the block; every thread gets
 // the result.  `red` holds kGenWarps * 4 entries.
@@ -317,13 +318,20 @@ int grid_for(long long n, int block) {
 }
 
 int device_sm_count() {
-    if (g_sm_count <= 0) {
-        int dev = 0, n = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
-        g_sm_count = n;
-    }
-    return g_sm_count;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int *slot = dev < kMaxDevices ? &g_sm_count[dev] : nullptr;
+    if (slot && *slot > 0) return *slot;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    if (slot) *slot = n;
+    return n;
+}
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    return dev;
 }
 
 int padded_labels(int M) {

@@ -133,7 +133,9 @@ cudaError_t launch_beliefs_f32(const float *g, const float *planes, GridDims d, 
 cudaError_t launch_beliefs_i32(const int32_t *e, const int32_t *planes, GridDims d, int32_t *out,
                                int32_t *map, cudaStream_t s);
 
-int device_sm_count();
+constexpr int kMaxDevices = 64;   // per-device caches are indexed by ordinal below this
+int device_sm_count();           // SMs of the current device (cached per device)
+int current_device();            // cudaGetDevice, 0 on error
 int grid_for(long long n, int block);   // blocks for a grid-stride elementwise kernel
 
 }  // namespace bpg

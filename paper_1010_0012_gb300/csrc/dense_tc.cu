@@ -663,14 +663,18 @@ struct TcState {
 };
 
 template <int MP>
-cudaError_t launch_gemm(const TcState &st, float *out, long long rows, int *status, cudaStream_t s) {
+cudaError_t launch_gemm(const TcState &st, float *out, long long rows, int *status, cudaStream_t s,
+                        bool set_attr_always = false) {
     using Cfg = TcCfg<MP>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the attribute belongs to the device's copy of the kernel: set it once per
+    // device (or on every call, for a caller that must survive a context change)
+    static bool attr_set[bpg::kMaxDevices] = {};
+    const int dev = bpg::current_device();
+    if (set_attr_always || dev >= bpg::kMaxDevices || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(dense_tc_gemm_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Cfg::kSmem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev < bpg::kMaxDevices) attr_set[dev] = true;
     }
     const long long tiles = (rows + kTileM - 1) / kTileM;
     int grid = bpg::device_sm_count();
@@ -683,12 +687,14 @@ template <int MP>
 cudaError_t launch_fused(const TcState &st, const float *g, const float *in, float *out, const bpg::GridDims &d,
                          int *status, cudaStream_t s) {
     using Cfg = FusedCfg<MP>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the attribute belongs to the device's copy of the kernel: set it once per device
+    static bool attr_set[bpg::kMaxDevices] = {};
+    const int dev = bpg::current_device();
+    if (dev >= bpg::kMaxDevices || !attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(dense_tc_fused_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Cfg::kSmem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev < bpg::kMaxDevices) attr_set[dev] = true;
     }
     const long long tiles = ((long long)d.W * d.H + kFusedNodes - 1) / kFusedNodes;
     int grid = bpg::device_sm_count();
@@ -783,10 +789,46 @@ namespace {
 constexpr size_t kNoAllocRowBytes = (size_t)32 << 20;          // packed h rows: at most 32 MiB
 constexpr size_t kNoAllocBBytes = (size_t)128 * 128 * 2;       // F^T, BF16, M <= 128
 constexpr size_t kNoAllocBytes = kNoAllocRowBytes + kNoAllocBBytes + 256;
-constexpr int kNoAllocMaxDevices = 64;
 
+// The array's device address, looked up with the device current.  The host-side
+// name of the array is only a stand-in, so the address comes from
+// cudaGetSymbolAddress.  It is cached per device ordinal together with the
+// unique ID of the context it was taken in (cuCtxGetId: never reused within a
+// process).  A cudaDeviceReset, or another context made current on the same
+// ordinal, changes that ID, and the address is looked up again.
 std::mutex g_noalloc_mu;
-uint8_t *g_noalloc_base[kNoAllocMaxDevices];   // device address of the array, per device
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    uint8_t *base;
+};
+NoAllocSlot g_noalloc_slot[bpg::kMaxDevices];
+
+typedef CUresult (*PFN_ctxGetCurrent)(CUcontext *);
+typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long *);
+
+// ID of the context current on this thread (0 when it cannot be read: then the
+// address is looked up on every call)
+unsigned long long current_ctx_id() {
+    static PFN_ctxGetCurrent get_cur = nullptr;
+    static PFN_ctxGetId get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = (PFN_ctxGetCurrent)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PFN_ctxGetId)p;
+        tried = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 struct NoAllocTable {
     float f[256];   // f(d), d = -T..T (T <= 127)
@@ -824,14 +866,22 @@ extern "C" bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const floa
     if (M != 64 && M != 128) return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: M must be 64 or 128");
     if (!dev_unary || !dev_in_planes || !dev_out_planes || !host_table)
         return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: NULL pointer");
-    if (dev_in_planes == dev_out_planes)
-        return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: input and output planes must differ");
+    // the kernels move 16-byte vectors: a view at an odd offset into a buffer
+    // would be a misaligned access on the device, so it is an argument error here
+    if ((((uintptr_t)dev_unary) | ((uintptr_t)dev_in_planes) | ((uintptr_t)dev_out_planes)) & 15u)
+        return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: device pointers must be 16-byte aligned");
     if (T < 0 || !(fbar >= 0) || !std::isfinite(fbar))
         return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: need T >= 0 and a finite fbar >= 0");
     const long long rows = 4LL * W * H;
     if ((long long)W * H > (1LL << 30) || (size_t)rows * M * 2 > kNoAllocRowBytes)
         return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: 4*W*H*M*2 bytes of packed rows exceed the "
                                         "fixed 32 MiB scratch (use bp_iterate_dense on a handle instead)");
+    {
+        const uintptr_t plane_bytes = (uintptr_t)rows * M * sizeof(float);
+        const uintptr_t a0 = (uintptr_t)dev_in_planes, b0 = (uintptr_t)dev_out_planes;
+        if (a0 < b0 + plane_bytes && b0 < a0 + plane_bytes)
+            return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: input and output planes overlap");
+    }
     NoAllocTable tab;
     tab.T = std::min(T, M - 1);
     tab.fbar = (float)fbar;
@@ -841,25 +891,37 @@ extern "C" bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const floa
             return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: table entries must be finite and >= 0");
         tab.f[d + tab.T] = v;
     }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    {
+        // the call ends with a stream synchronisation, so it cannot be captured
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaError_t ec = cudaStreamIsCapturing(s, &cap);
+        if (ec != cudaSuccess)
+            return noalloc_fail(BP_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ec));
+        if (cap != cudaStreamCaptureStatusNone)
+            return noalloc_fail(BP_ERR_STATE, "bp_iterate_dense_tc_noalloc: the stream is being captured; this call "
+                                              "synchronises its stream and cannot be captured");
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(BP_ERR_UNSUPPORTED, "device index out of range");
+    if (dev < 0 || dev >= bpg::kMaxDevices) return noalloc_fail(BP_ERR_UNSUPPORTED, "device index out of range");
     uint8_t *base = nullptr;
     {
-        // once per device, with that device current: the host-side name of the
-        // array is not a device address, so ask the runtime for the address
+        // set-up, once per device and context, with that device current
+        const unsigned long long ctx = current_ctx_id();
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_base[dev]) {
+        NoAllocSlot &slot = g_noalloc_slot[dev];
+        if (!slot.base || ctx == 0 || slot.ctx_id != ctx) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, bpg_noalloc_scratch);
             if (e != cudaSuccess)
                 return noalloc_fail(BP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_noalloc_base[dev] = (uint8_t *)p;
+            slot.base = (uint8_t *)p;
+            slot.ctx_id = ctx;
         }
-        base = g_noalloc_base[dev];
+        base = slot.base;
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     __nv_bfloat16 *A = (__nv_bfloat16 *)base;
     __nv_bfloat16 *B = (__nv_bfloat16 *)(base + kNoAllocRowBytes);
     int *status = (int *)(base + kNoAllocRowBytes + kNoAllocBBytes);
@@ -876,8 +938,8 @@ extern "C" bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const floa
     if (!make_map(&st.map_a, A, (unsigned long long)rows, (unsigned long long)M, kTileM) ||
         !make_map(&st.map_b, B, (unsigned long long)M, (unsigned long long)M, (unsigned)M))
         return noalloc_fail(BP_ERR_CUDA, "bp_iterate_dense_tc_noalloc: cuTensorMapEncodeTiled failed");
-    e = M == 128 ? launch_gemm<128>(st, dev_out_planes, rows, status, s)
-                 : launch_gemm<64>(st, dev_out_planes, rows, status, s);
+    e = M == 128 ? launch_gemm<128>(st, dev_out_planes, rows, status, s, true)
+                 : launch_gemm<64>(st, dev_out_planes, rows, status, s, true);
     if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("GEMM launch: ") + cudaGetErrorString(e));
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return noalloc_fail(BP_ERR_CUDA, std::string("iteration: ") + cudaGetErrorString(e));

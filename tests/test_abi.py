@@ -111,3 +111,31 @@ def test_binding_names_match_the_abi():
     defined = {n.name for n in ast.parse(src).body if isinstance(n, ast.FunctionDef)}
     missing = [n for n in declared_functions() if n not in defined]
     assert not missing, missing
+
+
+def test_no_alloc_entry_point_checks_pointers_before_touching_a_device(lib):
+    """bp_iterate_dense_tc_noalloc refuses misaligned and overlapping device
+    ranges on the host, before any CUDA call, so the addresses here are never
+    dereferenced."""
+    import numpy as np
+    fn = lib.bp_iterate_dense_tc_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    lib.bp_last_error.restype = ctypes.c_char_p
+    lib.bp_last_error.argtypes = [ctypes.c_void_p]
+    tab = np.ones(7, dtype=np.float32)
+    tp = tab.ctypes.data_as(ctypes.c_void_p)
+    W, H, M = 8, 8, 64
+    nbytes = 4 * W * H * M * 4
+    base = 1 << 40
+    assert fn(W, H, M, base, base + 2 * nbytes, base + 4 * nbytes + 4, tp, 3, 0.2, None) == 1
+    assert b"aligned" in lib.bp_last_error(None)
+    assert fn(W, H, M, base + 8, base + 2 * nbytes, base + 4 * nbytes, tp, 3, 0.2, None) == 1
+    assert b"aligned" in lib.bp_last_error(None)
+    assert fn(W, H, M, base, base + 2 * nbytes, base + 2 * nbytes + nbytes // 2, tp, 3, 0.2, None) == 1
+    assert b"overlap" in lib.bp_last_error(None)
+    assert fn(W, H, M, base, base + 2 * nbytes, base + 2 * nbytes, tp, 3, 0.2, None) == 1
+    assert b"overlap" in lib.bp_last_error(None)
+    assert fn(W, H, 32, base, base + 2 * nbytes, base + 4 * nbytes, tp, 3, 0.2, None) == 1
+    assert fn(W, H, M, base, base + 2 * nbytes, base + 4 * nbytes, None, 3, 0.2, None) == 1
