@@ -48,6 +48,8 @@ def parse_args():
                     help="skip the FP32 O(mM) vs O(M^2) comparison on the host cores")
     ap.add_argument("--no-baselines", action="store_true", help="skip the O(M^2) baselines")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 384x288, 64-MRF batch and gradient workloads in the default line")
     ap.add_argument("--persistent", type=int, default=-1, choices=[-1, 0, 1],
                     help="issue form of single-grid iterations (see bp_set_persistent)")
     ap.add_argument("--rows", type=int, default=0,
@@ -220,6 +222,61 @@ def cpu_throughput_sample(cfg, stereo_obj, rows=180, reps=3):
                       f"median of {reps}"}
 
 
+# Algorithmic HBM bytes per message update of each update kind: read the unary
+# and the four incoming messages, write the four outgoing ones (9 bytes at
+# FP32); the packed tensor-core form also writes its BF16 h rows (8 bytes per
+# node-label) and reads them back in the GEMM: 7 + 6 = 13 bytes per update.
+UPDATE_BYTES = {"band_mM": 9.0, "dense_bf16_tcgen05_fused": 9.0, "dense_bf16_tcgen05": 13.0,
+                "dense_fp32_cuda_core": 9.0}
+
+
+def time_updates_median(G, stream, cfg, dev, kinds, reps=5):
+    """Per-iteration time of each update kind on the handle's grid: one
+    warm-up call, then `reps` timed calls of n iterations each (CUDA events on
+    the handle's stream), median of the repetitions."""
+    import torch
+    from paper_1010_0012_gb300 import bp
+    pk = peaks()
+    units = workload_units(cfg)
+    res = {}
+    with ClockSampler(dev) as clk:
+        clk.wait_ready()
+        for name, kind in kinds:
+            n_it = 3 if kind == bp.BP_DENSE_CUDA_CORE else 20
+            if kind is None:
+                fn = (lambda k: (lambda: G.iterate(k, bp.BP_SUM, "sync")))(n_it)
+            else:
+                fn = (lambda k, n: (lambda: bp.bp_iterate_dense(G.h, n, k)))(kind, n_it)
+            try:
+                G.reset()
+                G.iterate(0, bp.BP_SUM, "sync")
+                fn()
+                G.sync()
+                ts = []
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    b.record(stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b) / 1e3 / n_it)
+                G.sync()
+                t = statistics.median(ts)
+                ach = units * UPDATE_BYTES[name] / t / 1e9
+                res[name] = {"value": units / t, "unit": UNIT, "ms_per_iter": t * 1e3,
+                             "ms_per_iter_min_max": [min(ts) * 1e3, max(ts) * 1e3],
+                             "timing": f"median of {reps} repetitions of {n_it} iterations (CUDA events)",
+                             "roofline": {"bound": "hbm", "bytes_per_update": UPDATE_BYTES[name], "achieved": ach,
+                                          "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                                          "peak_source": pk["source"]}}
+            except bp.BPError as e:
+                res[name] = {"unavailable": str(e)[:160]}
+    res["clocks"] = clk.summary()
+    if "value" in res.get("band_mM", {}) and "value" in res.get("dense_bf16_tcgen05_fused", {}):
+        res["band_over_fused_tcgen05"] = res["band_mM"]["value"] / res["dense_bf16_tcgen05_fused"]["value"]
+    return res
+
+
 # ------------------------------------------------------------------ GPU arm ----
 
 def aggregate_over_ranks(elapsed_s, units_local, world, device=None):
@@ -363,27 +420,15 @@ def run_ours(args, cfg, rank, world):
         G.set_unary(g_dev)
         torch.cuda.synchronize()
 
-    # O(M^2) baselines on the same grid and state, timed per iteration
+    # O(M^2) baselines on the same grid and state, timed per iteration: each
+    # update (the O(mM) one included, so the ratio is taken under the same
+    # conditions) runs `reps` repetitions of `n_it` iterations after a warm-up
+    # call; the median repetition is reported, with the clocks of the region.
     if not args.no_baselines:
-        base = {}
-        for name, kind in (("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE), ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC),
-                           ("dense_bf16_tcgen05_fused", bp.BP_DENSE_BF16_TC_FUSED)):
-            try:
-                G.reset()
-                n_it = 3
-                bp.bp_iterate_dense(G.h, 1, kind)
-                G.sync()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                bp.bp_iterate_dense(G.h, n_it, kind)
-                b.record(stream)
-                b.synchronize()
-                G.sync()
-                s = a.elapsed_time(b) / 1e3 / n_it
-                base[name] = {"value": workload_units(cfg) / s, "unit": UNIT, "ms_per_iter": s * 1e3}
-            except bp.BPError as e:
-                base[name] = {"unavailable": str(e)[:160]}
-        out["baselines"] = base
+        out["baselines"] = time_updates_median(
+            G, stream, cfg, dev,
+            [("band_mM", None), ("dense_bf16_tcgen05_fused", bp.BP_DENSE_BF16_TC_FUSED),
+             ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC), ("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE)])
     G.close()
     return out
 
@@ -403,15 +448,15 @@ def _event_time(stream, fn, reps=1):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def run_batch_workload(args):
-    """64 MRFs of uneven size / labels / band, 30 iterations per step, one
-    persistent launch per step; min-sum int32 and sum-product FP32."""
+def measure_batch(args, n=64, K=30):
+    """64 MRFs of uneven size / labels / band, K iterations per step, one
+    persistent launch per step; min-sum int32 and sum-product FP32.  Returns
+    (per-mode results, workload description)."""
     import torch
     from paper_1010_0012_gb300 import bp
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    n = 64 if not args.rows else max(2, args.rows)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
     items = wl.make_batch(n=n)
-    K = 30
     units = sum(wl.directed_edges(it.cfg.W, it.cfg.H) * it.cfg.M for it in items) * K
     bytes_it = sum((it.cfg.W * it.cfg.H * it.cfg.M + 2 * wl.directed_edges(it.cfg.W, it.cfg.H) * it.cfg.M) * 4
                    for it in items)
@@ -433,7 +478,7 @@ def run_batch_workload(args):
         b = bp.bp_batch_create(descs, dtype, stream=stream)
         del keep
         tune_ms = bp.bp_batch_autotune(b, mode, 8)
-        fam, tile = bp.bp_batch_get_tiling(b)
+        tiling = bp.bp_batch_get_tiling(b)
 
         def step():
             bp.bp_batch_reset_messages(b)
@@ -443,27 +488,33 @@ def run_batch_workload(args):
             step()
         bp.bp_batch_sync(b)
         l0 = bp.bp_batch_launch_count(b)
-        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        with ClockSampler(dev) as clk:
             clk.wait_ready()
             t = _event_time(stream, step, args.steps)
         bp.bp_batch_sync(b)
         launches = bp.bp_batch_launch_count(b) - l0
         ach = bytes_it * K / t / 1e9
-        res[mode_name] = {"value": units / t, "unit": UNIT, "ms_per_step": t * 1e3, "tiling": [fam, tile],
+        res[mode_name] = {"value": units / t, "unit": UNIT, "ms_per_step": t * 1e3, "tiling": tiling,
                           "autotune_ms_per_iter": tune_ms, "gpu_launches": launches,
-                          "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                                       "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"]},
+                          "roofline": {"bound": "hbm", "kernel": "batch_kernel (persistent, all MRFs)",
+                                       "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                       "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"],
+                                       "algorithmic_bytes_per_iteration": bytes_it},
                           "clocks": clk.summary()}
         bp.bp_batch_destroy(b)
         torch.cuda.empty_cache()
+    desc = (f"batch of {n} MRFs, W 128..640, H 128..480, M in 32/64/128/256, T 2..8, {K} synchronous iterations "
+            "per step, one persistent launch")
+    return res, {"workload": desc, "algorithmic_bytes_per_iteration": bytes_it, "units_per_step": units}
+
+
+def run_batch_workload(args):
+    n = 64 if not args.rows else max(2, args.rows)
+    res, config = measure_batch(args, n=n)
     line = {"metric": METRIC + " (batch of uneven MRFs)", "value": res["min_i32"]["value"], "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["min_i32"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-            "config": {"workload": f"batch of {n} MRFs, W 128..640, H 128..480, M in 32/64/128/256, T 2..8, "
-                                   f"{K} synchronous iterations per step, one persistent launch",
-                       "algorithmic_bytes_per_iteration": bytes_it, "units_per_step": units},
-            "modes": res}
+            "vs_baseline": None, "dtype": "i32", "data": "synthetic", "config": config, "modes": res}
     print(json.dumps(line))
 
 
@@ -554,8 +605,9 @@ def l2_copy_probe(stream, mb=16, reps=200):
                    "CUDA events"}
 
 
-def run_grid_workload(args, name):
-    """A single grid in both modes on its own schedule (e.g. 384x288 red-black)."""
+def measure_grid(args, name):
+    """A single grid in both modes on its own schedule (e.g. 384x288 red-black).
+    Returns (per-mode results, workload description)."""
     import torch
     from paper_1010_0012_gb300 import bp
     cfg = wl.CONFIGS[name]
@@ -584,13 +636,17 @@ def run_grid_workload(args, name):
         for _ in range(args.warmup):
             step()
         G.sync()
-        t = _event_time(stream, step, args.steps)
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            clk.wait_ready()
+            t = _event_time(stream, step, args.steps)
         G.sync()
         ach = algorithmic_bytes(cfg) * cfg.iters / t / 1e9
         res[mode_name] = {"value": units / t, "unit": UNIT, "ms_per_step": t * 1e3,
+                          "layout": list(bp.bp_get_layout(G.h)),
                           "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                                       "frac": ach / pk["hbm_gbs"],
-                                       "note": "working set fits in L2 when small: frac may exceed 1"}}
+                                       "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"],
+                                       "note": "working set fits in L2 when small: frac may exceed 1"},
+                          "clocks": clk.summary()}
         G.close()
     state_bytes = (cfg.W * cfg.H * cfg.M * 4) * (9 if cfg.schedule == "sync" else 5)
     if state_bytes < 64 << 20:
@@ -599,22 +655,50 @@ def run_grid_workload(args, name):
         probe = l2_copy_probe(stream)
         for r in res.values():
             r["roofline"]["l2_probe"] = dict(probe, frac=r["roofline"]["achieved"] / probe["copy_gbs"])
+    desc = f"{cfg.name}: {cfg.W}x{cfg.H}, M={cfg.M}, T={cfg.T}, {cfg.iters} {cfg.schedule} iterations per step"
+    return res, {"workload": desc}
+
+
+def run_grid_workload(args, name):
+    res, config = measure_grid(args, name)
     first = next(iter(res.values()))
     line = {"metric": METRIC, "value": first["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": first["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{cfg.name}: {cfg.W}x{cfg.H}, M={cfg.M}, T={cfg.T}, {cfg.iters} {cfg.schedule} "
-                                   "iterations per step"}, "modes": res}
+            "config": config, "modes": res}
     print(json.dumps(line))
 
 
-def run_gradient_workload(args):
+def gradient_floor_bytes(cfg, every=5):
+    """HBM bytes the checkpointed gradient's launches must move: the recorded
+    forward (K log-domain iterations at 9 bytes per update), the checkpoint
+    copies (read and write one message state each), the recomputed states of
+    every segment (K minus one per segment) and K adjoint launches at 15 bytes
+    per node-label-direction (read l, log g, the adjoint in and d log g; write
+    the adjoint out and d log g).  Beliefs and their reverse are left out (one
+    launch each, under 2 %)."""
+    nodes = cfg.W * cfg.H
+    De = wl.directed_edges(cfg.W, cfg.H)
+    K = cfg.iters
+    n_ck = (K + every - 1) // every
+    fwd = (nodes * cfg.M + 2 * De * cfg.M) * 4
+    adj = nodes * cfg.M * 15 * 4
+    state = 4 * nodes * cfg.M * 4
+    parts = {"forward": K * fwd, "checkpoints": n_ck * 2 * state, "recompute": (K - n_ck) * fwd,
+             "adjoint": K * adj}
+    return sum(parts.values()), parts
+
+
+def measure_gradient(args, every=5):
     """Loss and gradient (alpha, fbar, beta) of 30 unrolled log-domain
-    iterations on 256x256, M=64, T=3, checkpoint every 5."""
+    iterations on 256x256, M=64, T=3, checkpoint every 5.  Wall-clock time per
+    gradient (the call a user makes: forward, loss, backward, gradients read
+    back to the host), against the byte floor of its launches."""
     import torch
     from paper_1010_0012_gb300 import autograd, bp
     cfg = wl.CONFIGS["grid256_m64_grad"]
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
     st = wl.make_stereo(cfg)
     cost = torch.from_numpy(st.cost.astype(np.float32)).cuda()
     gt = torch.as_tensor(st.d_gt, dtype=torch.long).cuda()
@@ -627,24 +711,43 @@ def run_gradient_workload(args):
         a = torch.tensor(cfg.alpha, requires_grad=True)
         fb = torch.tensor(float(np.exp(-cfg.alpha * cfg.T)), requires_grad=True)
         be = beta0.clone().requires_grad_(True)
-        loss = autograd.stereo_nll(cost, gt, a, fb, be, cfg.T, cfg.iters, G, 5)
+        loss = autograd.stereo_nll(cost, gt, a, fb, be, cfg.T, cfg.iters, G, every)
         loss.backward()
         return float(a.grad)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize()
-    t = (time.perf_counter() - t0) / args.steps
-    units = workload_units(cfg) * cfg.iters
-    line = {"metric": "gradient evaluations/s (forward + adjoint, 30 unrolled iterations)", "value": 1.0 / t,
-            "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "256x256, M=64, T=3, 30 log-domain iterations, checkpoint 5, loss -sum log b(gt)",
-                       "forward_message_updates_per_s": units / t}}
+    l0 = G.launches
+    with ClockSampler(dev) as clk:
+        clk.wait_ready()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) / args.steps
+    launches = G.launches - l0
     G.close()
+    pk = peaks()
+    floor, parts = gradient_floor_bytes(cfg, every)
+    ach = floor / t / 1e9
+    return {"value": 1.0 / t, "unit": "gradients/s", "ms_per_gradient": t * 1e3,
+            "forward_message_updates_per_s": workload_units(cfg) * cfg.iters / t,
+            "gpu_launches_per_gradient": launches / max(1, args.steps),
+            "roofline": {"bound": "hbm", "kernel": "whole gradient (log forward, checkpoints, recompute, adjoint)",
+                         "algorithmic_bytes_per_gradient": floor, "bytes_by_part": parts,
+                         "floor_ms": floor / (pk["hbm_gbs"] * 1e9) * 1e3, "achieved": ach, "peak": pk["hbm_gbs"],
+                         "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"]},
+            "clocks": clk.summary(), "timing": f"wall clock over {args.steps} gradients after {args.warmup}"}, {
+        "workload": "256x256, M=64, T=3, 30 log-domain iterations, checkpoint 5, loss -sum log b(gt); "
+                    "gradients wrt alpha, fbar, beta"}
+
+
+def run_gradient_workload(args):
+    res, config = measure_gradient(args)
+    line = {"metric": "gradient evaluations/s (forward + adjoint, 30 unrolled iterations)", "value": res["value"],
+            "unit": "gradients/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms_per_gradient"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "result": res}
     print(json.dumps(line))
 
 
@@ -891,6 +994,22 @@ def main():
         line["e2e_unary_upload"] = res["e2e_unary_upload"]
     if "baselines" in res:
         line["baselines"] = res["baselines"]
+    if not args.no_secondary and world == 1:
+        # the other workloads of the hot path, each with its own roofline and
+        # clocks: the 384x288 red-black grid (both modes), the 64-MRF batch
+        # (both modes) and the checkpointed gradient
+        sec_args = argparse.Namespace(**vars(args))
+        sec_args.steps, sec_args.warmup = max(3, min(args.steps, 10)), max(3, min(args.warmup, 3))
+        sec = {}
+        for key, fn in (("grid384x288_m16", lambda: measure_grid(sec_args, "grid384x288_m16")),
+                        ("batch64", lambda: measure_batch(sec_args)),
+                        ("grid256_m64_grad", lambda: measure_gradient(sec_args))):
+            try:
+                r, c = fn()
+                sec[key] = {"config": c, "steps": sec_args.steps, "warmup": sec_args.warmup, "result": r}
+            except Exception as e:      # a failed secondary line must not lose the headline
+                sec[key] = {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+        line["secondary"] = sec
     if not args.no_cpu_baseline:
         st = wl.make_stereo(cfg)
         v, desc, t = oracle_sample(cfg, st, target_s=10.0)

@@ -57,3 +57,27 @@ def test_algorithmic_bytes_and_units_of_the_benchmark_workload():
     assert De == 2 * (720 * 1279 + 1280 * 719)
     assert bench.workload_units(cfg) == De * 128
     assert bench.algorithmic_bytes(cfg) == (1280 * 720 * 128 + 2 * De * 128) * 4 == 4242636800
+
+
+def test_gradient_floor_counts_each_launch_of_the_checkpointed_schedule():
+    """256x256, M = 64, K = 30, checkpoint 5: 30 recorded and 24 recomputed
+    forward launches at (W H M + 2 De M) * 4 bytes, 30 adjoint launches at
+    15 words per node-label, 6 checkpoint copies of a 4-plane state."""
+    import bench
+    from paper_1010_0012_gb300 import workload as wl
+    cfg = wl.CONFIGS["grid256_m64_grad"]
+    total, parts = bench.gradient_floor_bytes(cfg, 5)
+    De = 2 * (256 * 255 + 256 * 255)
+    fwd = (256 * 256 * 64 + 2 * De * 64) * 4
+    assert fwd == 150_470_656
+    assert parts["forward"] == 30 * fwd and parts["recompute"] == 24 * fwd
+    assert parts["adjoint"] == 30 * 256 * 256 * 64 * 60
+    assert parts["checkpoints"] == 6 * 2 * 4 * 256 * 256 * 64 * 4
+    assert total == sum(parts.values())
+
+
+def test_update_bytes_of_the_dense_forms():
+    import bench
+    assert bench.UPDATE_BYTES["band_mM"] == 9.0
+    assert bench.UPDATE_BYTES["dense_bf16_tcgen05_fused"] == 9.0
+    assert bench.UPDATE_BYTES["dense_bf16_tcgen05"] == 13.0
