@@ -835,19 +835,32 @@ def run_sparse_workload(args):
             G.reset()
             G.iterate(0, mode)
             G.iterate(10, mode)
-        for _ in range(args.warmup):
-            step()
-        G.sync()
-        t = _event_time(stream, step, args.steps)
-        G.sync()
-        ach = algorithmic_bytes(cfg) * 10 / t / 1e9
-        res[name] = {"value": units / t, "unit": UNIT, "ms_per_iter": t * 1e2,
-                     "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                                  "frac": ach / pk["hbm_gbs"]}}
+        res[name] = {}
+        for kname, kind in (("registers", bp.BP_SPARSE_REGISTERS), ("lists", bp.BP_SPARSE_LISTS)):
+            try:
+                bp.bp_set_sparse_kernel(G.h, kind)
+            except bp.BPError as e:
+                res[name][kname] = {"unavailable": str(e)[:160]}
+                continue
+            _, steps_, wf = bp.bp_get_sparse_kernel(G.h)
+            for _ in range(args.warmup):
+                step()
+            G.sync()
+            with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+                clk.wait_ready()
+                t = _event_time(stream, step, args.steps)
+            G.sync()
+            ach = algorithmic_bytes(cfg) * 10 / t / 1e9
+            res[name][kname] = {"value": units / t, "unit": UNIT, "ms_per_iter": t * 1e2,
+                                "schedule": {"steps": steps_, "gather_wavefronts_per_node": wf},
+                                "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                                             "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                                             "peak_source": pk["source"]},
+                                "clocks": clk.summary()}
         G.close()
         del u
     line = {"metric": METRIC + " (general sparse compatibility, 9 pairs per label)",
-            "value": res["sum_f32"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "value": res["sum_f32"]["registers"].get("value", res["sum_f32"]["lists"].get("value")), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{cfg.W}x{cfg.H}, M={cfg.M}, random non-difference pattern, 10 synchronous "
                                    "iterations"},

@@ -129,7 +129,8 @@ bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fb
  * costs O(nnz) with nnz = rowptr[M] (O(mM) for m pairs per label).  Replaces
  * any band potential; BP_ERR_POTENTIAL in max mode if some E > Ebar;
  * BP_ERR_UNSUPPORTED for M > 512.  The pattern is copied to the device (8
- * bytes per receiver label per entry of the longest list).  Log mode and
+ * bytes per receiver label per entry of the longest list), and, where it fits
+ * the register kernel (bp_set_sparse_kernel), scheduled on the host for it.  Log mode and
  * bp_backward need a band potential. */
 bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
                                   const void *host_vals, double fbar);
@@ -331,6 +332,41 @@ void bp_batch_destroy(bp_batch b);
  *    size (CUDA-graph replay of per-iteration launches beats the persistent
  *    kernel's grid barrier even on 32 x 32 grids).  Results are identical. */
 bp_status bp_set_persistent(bp_handle h, int mode);
+
+/* Which kernel runs a general sparse-compatibility potential (no counterpart
+ * in the paper; both compute Sec. 4's O(nnz) form of Eq. 7 / Eq. 11 and give
+ * the same messages up to the order of the terms of each sum):
+ *   BP_SPARSE_LISTS      per-label entry lists read from the device for
+ *                        every node (any pattern, M <= 512);
+ *   BP_SPARSE_REGISTERS  the pattern held in registers for the whole launch,
+ *                        its entries scheduled on the host so that the
+ *                        shared-memory gathers do not conflict (M <= 256 and
+ *                        a schedule of at most 48, 24, 12 or 6 steps per
+ *                        32-label block for M <= 32, 64, 128, 256);
+ *   BP_SPARSE_AUTO       (default) the register kernel where the pattern has
+ *                        a schedule, else the lists.
+ * bp_set_sparse_kernel returns BP_ERR_UNSUPPORTED when the current pattern has
+ * no register schedule and BP_SPARSE_REGISTERS is asked for.
+ * bp_get_sparse_kernel reports the kernel that runs, and for the register
+ * kernel the steps per block and the gather wavefronts per node of the
+ * schedule (0 for the lists); BP_ERR_STATE without a sparse potential. */
+typedef enum { BP_SPARSE_AUTO = 0, BP_SPARSE_LISTS = 1, BP_SPARSE_REGISTERS = 2 } bp_sparse_kernel;
+bp_status bp_set_sparse_kernel(bp_handle h, int kind);
+bp_status bp_get_sparse_kernel(bp_handle h, int *kind, int *steps, int *wavefronts);
+
+/* The register kernel's schedule of a pattern, computed on the host only (no
+ * device, no handle; no counterpart in the paper).  Pattern as for
+ * bp_set_potential_sparse (CSR by receiver label, M labels).  *KM = 32-label
+ * receiver blocks, *LM = register steps per block, *steps = the longest
+ * quarter-warp schedule, *wavefronts = gather wavefronts per node; all 0 when
+ * the pattern has no register schedule.  host_lab [KM][32] (nullable)
+ * receives each lane's receiver label (-1: none); host_ent [KM][LM][32][2]
+ * (nullable) each lane's entry per step: the byte offset of the sender label's
+ * h slot (0xFFFF for a hole) and the entry's CSR position in host_cols.
+ * Call with NULL buffers first to learn KM and LM.  Errors through
+ * bp_last_error(NULL). */
+bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int *KM, int *LM,
+                             int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent);
 
 /* ---- factor graphs with three-variable factors (Sec. 7) --------------------
  * Variables v = 0..n_vars-1 with M labels and unaries g_v (or energies E_v);

@@ -22,6 +22,7 @@ BP_SUM, BP_MAX, BP_LOG, BP_RECORD = 0, 1, 2, 4
 BP_SYNC, BP_REDBLACK = 0, 1
 BP_F32, BP_I32 = 0, 1
 BP_DENSE_CUDA_CORE, BP_DENSE_BF16_TC, BP_DENSE_BF16_TC_FUSED = 0, 1, 2
+BP_SPARSE_AUTO, BP_SPARSE_LISTS, BP_SPARSE_REGISTERS = 0, 1, 2
 STATUS_NAMES = {0: "BP_OK", 1: "BP_ERR_ARG", 2: "BP_ERR_STATE", 3: "BP_ERR_CUDA", 4: "BP_ERR_OOM",
                 5: "BP_ERR_POTENTIAL", 6: "BP_ERR_TIMEOUT", 7: "BP_ERR_UNSUPPORTED"}
 SCHEDULES = {"sync": BP_SYNC, "redblack": BP_REDBLACK}
@@ -55,6 +56,9 @@ def _load():
         "bp_backward": ([P, P, P, P, P], I),
         "bp_set_checkpoint_interval": ([P, I], I),
         "bp_set_persistent": ([P, I], I),
+        "bp_set_sparse_kernel": ([P, I], I),
+        "bp_get_sparse_kernel": ([P, P, P, P], I),
+        "bp_sparse_schedule": ([I, P, P, P, P, P, P, P, P], I),
         "bp_set_grid": ([P, I], I),
         "bp_sync": ([P], I),
         "bp_last_error": ([P], ctypes.c_char_p),
@@ -247,6 +251,38 @@ def bp_set_grid(h, blocks):
 
 def bp_set_persistent(h, mode):
     _check(h, _lib.bp_set_persistent(h, int(mode)))
+
+
+def bp_set_sparse_kernel(h, kind):
+    _check(h, _lib.bp_set_sparse_kernel(h, int(kind)))
+
+
+def bp_sparse_schedule(M, rowptr, cols):
+    """The register kernel's schedule of a CSR pattern (host only): dict with
+    KM, LM, steps, wavefronts, lab [KM][32] and ent [KM][LM][32][2] (byte
+    offset of the h slot or 0xFFFF, CSR position), or None without one."""
+    import numpy as np
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    cl = np.ascontiguousarray(cols, dtype=np.int32)
+    v = [ctypes.c_int() for _ in range(4)]
+    vp = rp.ctypes.data_as(ctypes.c_void_p)
+    cp = cl.ctypes.data_as(ctypes.c_void_p) if cl.size else None
+    _check(None, _lib.bp_sparse_schedule(int(M), vp, cp, *[ctypes.byref(x) for x in v], None, None))
+    KM, LM, steps, wf = (x.value for x in v)
+    if KM == 0:
+        return None
+    lab = np.empty((KM, 32), np.int32)
+    ent = np.empty((KM, LM, 32, 2), np.int32)
+    _check(None, _lib.bp_sparse_schedule(int(M), vp, cp, *[ctypes.byref(x) for x in v],
+                                         lab.ctypes.data_as(ctypes.c_void_p), ent.ctypes.data_as(ctypes.c_void_p)))
+    return {"KM": KM, "LM": LM, "steps": steps, "wavefronts": wf, "lab": lab, "ent": ent}
+
+
+def bp_get_sparse_kernel(h):
+    """(kernel in use, steps per block, gather wavefronts per node)."""
+    k, st, wf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(h, _lib.bp_get_sparse_kernel(h, ctypes.byref(k), ctypes.byref(st), ctypes.byref(wf)))
+    return k.value, st.value, wf.value
 
 
 def bp_sync(h):

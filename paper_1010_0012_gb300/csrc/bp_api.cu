@@ -127,6 +127,15 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
         cudaError_t e;
         if (h->sparse) {
             if (is_log) return cudaErrorNotSupported;
+            if (h->sp_reg && h->sp_kernel != BP_SPARSE_LISTS) {
+                SparseRegArgs a{h->unary, in, out, h->dims, parity, (const int2 *)h->d_sp_rent,
+                                (const int32_t *)h->d_sp_rlab, h->fbarf, h->ebar, h->d_status};
+                e = h->dtype == BP_I32 ? launch_sparse_reg_min(a, h->sp_KM, h->sp_LM, h->stream)
+                                       : launch_sparse_reg_sum(a, h->sp_KM, h->sp_LM, h->stream);
+                if (e != cudaSuccess) return e;
+                ++count;
+                continue;
+            }
             if (h->dtype == BP_I32) {
                 SparseArgsI a{(const int32_t *)h->unary, (const int32_t *)in, (int32_t *)out, h->dims, parity,
                               (const int32_t *)h->d_sp_len, (const int2 *)h->d_sp_ell, h->ebar};
@@ -386,7 +395,7 @@ void bp_destroy(bp_handle h) {
     clear_graphs(h);
     bpg_free_extras(h);
     void *bufs[] = {h->unary, h->log_unary, h->msg[0], h->msg[1], h->d_wf, h->d_wi, h->d_dense, h->d_status,
-                    h->tune_buf, h->d_sp_len, h->d_sp_ell, h->d_stereo};
+                    h->tune_buf, h->d_sp_len, h->d_sp_ell, h->d_sp_rent, h->d_sp_rlab, h->d_stereo};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -658,14 +667,33 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
             ell[((size_t)i * h->M + xj) * 2] = sp_label_slot(host_cols[p]);
             ell[((size_t)i * h->M + xj) * 2 + 1] = wbits[p];
         }
-    void *bufs[] = {h->d_sp_len, h->d_sp_ell};
+    // the register-pattern schedule, when the pattern fits one (else the list kernels serve)
+    SparseRegPlan plan;
+    const bool reg_ok = sparse_reg_plan(h->M, h->Mp, host_rowptr, host_cols, wbits.data(), &plan);
+    BP_CK(h, cudaStreamSynchronize(h->stream));   // earlier work may still read the old pattern
+    void *bufs[] = {h->d_sp_len, h->d_sp_ell, h->d_sp_rent, h->d_sp_rlab};
     for (void *p : bufs)
         if (p) cudaFree(p);
-    h->d_sp_len = h->d_sp_ell = nullptr;
+    h->d_sp_len = h->d_sp_ell = h->d_sp_rent = h->d_sp_rlab = nullptr;
+    h->sp_reg = false;
     if (bp_status st = ensure_buffer(h, &h->d_sp_len, (size_t)h->M * 4, "sparse row lengths")) return st;
     if (bp_status st = ensure_buffer(h, &h->d_sp_ell, ell.size() * 4, "sparse pattern")) return st;
     BP_CK(h, cudaMemcpyAsync(h->d_sp_len, len.data(), (size_t)h->M * 4, cudaMemcpyHostToDevice, h->stream));
     BP_CK(h, cudaMemcpyAsync(h->d_sp_ell, ell.data(), ell.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    if (reg_ok) {
+        if (bp_status st = ensure_buffer(h, &h->d_sp_rent, plan.ent.size() * 4, "register pattern")) return st;
+        if (bp_status st = ensure_buffer(h, &h->d_sp_rlab, plan.lab.size() * 4, "register pattern labels"))
+            return st;
+        BP_CK(h, cudaMemcpyAsync(h->d_sp_rent, plan.ent.data(), plan.ent.size() * 4, cudaMemcpyHostToDevice,
+                                 h->stream));
+        BP_CK(h, cudaMemcpyAsync(h->d_sp_rlab, plan.lab.data(), plan.lab.size() * 4, cudaMemcpyHostToDevice,
+                                 h->stream));
+        h->sp_reg = true;
+        h->sp_KM = plan.KM;
+        h->sp_LM = plan.LM;
+        h->sp_steps = plan.steps;
+        h->sp_wavefronts = plan.wavefronts;
+    }
     BP_CK(h, cudaStreamSynchronize(h->stream));
     if (h->d_dense) { cudaFree(h->d_dense); h->d_dense = nullptr; }
     h->sparse = true;
@@ -913,6 +941,56 @@ bp_status bp_set_grid(bp_handle h, int blocks) {
     h->err.clear();
     if (blocks < 0 || blocks > (1 << 20)) return fail(h, BP_ERR_ARG, "bp_set_grid: blocks out of range");
     h->blocks_override = blocks;
+    return BP_OK;
+}
+
+bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int *KM, int *LM,
+                             int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent) {
+    g_global_err.clear();
+    if (M < 2 || M > 1024) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: M out of range");
+    if (!host_rowptr || !KM || !LM || !steps || !wavefronts || (!host_cols && host_rowptr[M] != 0))
+        return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: NULL argument");
+    if (host_rowptr[0] != 0) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: rowptr[0] must be 0");
+    for (int x = 0; x < M; ++x)
+        if (host_rowptr[x + 1] < host_rowptr[x]) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: rowptr decreases");
+    for (int p = 0; p < host_rowptr[M]; ++p)
+        if (host_cols[p] < 0 || host_cols[p] >= M)
+            return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: column out of range");
+    std::vector<int32_t> index(host_rowptr[M]);
+    for (int p = 0; p < host_rowptr[M]; ++p) index[p] = p;
+    SparseRegPlan plan;
+    *KM = *LM = *steps = *wavefronts = 0;
+    if (!sparse_reg_plan(M, padded_labels(M), host_rowptr, host_cols, index.data(), &plan)) return BP_OK;
+    *KM = plan.KM;
+    *LM = plan.LM;
+    *steps = plan.steps;
+    *wavefronts = plan.wavefronts;
+    if (host_lab) std::memcpy(host_lab, plan.lab.data(), plan.lab.size() * 4);
+    if (host_ent) std::memcpy(host_ent, plan.ent.data(), plan.ent.size() * 4);
+    return BP_OK;
+}
+
+bp_status bp_set_sparse_kernel(bp_handle h, int kind) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_sparse_kernel: NULL handle");
+    h->err.clear();
+    if (kind != BP_SPARSE_AUTO && kind != BP_SPARSE_LISTS && kind != BP_SPARSE_REGISTERS)
+        return fail(h, BP_ERR_ARG, "bp_set_sparse_kernel: unknown kind");
+    if (kind == BP_SPARSE_REGISTERS && h->sparse && !h->sp_reg)
+        return fail(h, BP_ERR_UNSUPPORTED, "bp_set_sparse_kernel: this pattern has no register schedule");
+    h->sp_kernel = kind;
+    clear_graphs(h);
+    return BP_OK;
+}
+
+bp_status bp_get_sparse_kernel(bp_handle h, int *kind, int *steps, int *wavefronts) {
+    if (!h) return fail(nullptr, BP_ERR_ARG, "bp_get_sparse_kernel: NULL handle");
+    h->err.clear();
+    if (!kind || !steps || !wavefronts) return fail(h, BP_ERR_ARG, "bp_get_sparse_kernel: NULL argument");
+    if (!h->sparse) return fail(h, BP_ERR_STATE, "bp_get_sparse_kernel: no sparse potential set");
+    const bool reg = h->sp_reg && h->sp_kernel != BP_SPARSE_LISTS;
+    *kind = reg ? BP_SPARSE_REGISTERS : BP_SPARSE_LISTS;
+    *steps = reg ? h->sp_steps : 0;
+    *wavefronts = reg ? h->sp_wavefronts : 0;
     return BP_OK;
 }
 

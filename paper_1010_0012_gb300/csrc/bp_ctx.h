@@ -59,6 +59,11 @@ struct bp_ctx {
     std::vector<float> sp_valf;      // f(x_i, x_j)
     std::vector<int32_t> sp_vali;    // E(x_i, x_j)
     void *d_sp_len = nullptr, *d_sp_ell = nullptr;   // device pattern (see bp_sparse.h)
+    // register-pattern schedule (sparse_reg_plan.cu), when the pattern fits one
+    bool sp_reg = false;
+    int sp_KM = 0, sp_LM = 0, sp_steps = 0, sp_wavefronts = 0;
+    void *d_sp_rent = nullptr, *d_sp_rlab = nullptr;
+    int sp_kernel = 0;               // BP_SPARSE_AUTO / _LISTS / _REGISTERS
     uint8_t *d_stereo = nullptr;     // staging of host images for bp_set_unary_stereo (2 W H bytes)
 
     bpg::Layout layout{32, 1};

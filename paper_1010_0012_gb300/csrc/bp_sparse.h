@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "bp_internal.h"
 
 namespace bpg {
@@ -39,5 +41,43 @@ struct SparseArgsI {
 
 cudaError_t launch_sparse_sum(const SparseArgsF &a, cudaStream_t s);
 cudaError_t launch_sparse_min(const SparseArgsI &a, cudaStream_t s);
+
+// ---- register-pattern kernels (sparse_reg.cuh) ----------------------------
+// Lane l of 32-label receiver block k owns the receiver label lab[k][l] (-1:
+// none) and, for each step c < LM, the entry ent[k][c][l] = (byte offset of
+// the sender label's h slot, or 0xFFFF for a hole; bits of f - fbar, or E).
+struct SparseRegArgs {
+    const void *u;           // [H][W][Mp] g (float) or E_u (int32)
+    const void *in;          // [4][H][W][Mp] incoming messages
+    void *out;               // [4][H][W][Mp] updated messages
+    GridDims d;
+    int parity;
+    const int2 *ent;         // device [KM][LM][32]
+    const int32_t *lab;      // device [KM][32]
+    float fbar;
+    int32_t ebar;
+    int *status;             // device error word: 301 when a bounded wait gave up
+};
+
+// (KM, LM) pairs compiled: KM = 32-label receiver blocks (Mp <= 32 KM), LM =
+// register steps per block; LM ascending for each KM.
+constexpr int kSparseRegVariants[][2] = {{1, 16}, {1, 48}, {2, 12}, {2, 24}, {4, 6}, {4, 12}, {8, 6}};
+
+struct SparseRegPlan {
+    int KM = 0, LM = 0;
+    int steps = 0;                 // largest quarter-warp schedule (LM >= steps)
+    int wavefronts = 0;            // sum over quarter-warps of their steps: gather wavefronts per node
+    std::vector<int32_t> ent;      // [KM][LM][32][2]
+    std::vector<int32_t> lab;      // [KM][32]
+};
+
+// Schedules a pattern (CSR by receiver label; wbits = value bits per entry)
+// for the register kernels.  False when Mp > 256 or when the schedule needs
+// more steps than any compiled variant holds (the list kernels serve it).
+bool sparse_reg_plan(int M, int Mp, const int32_t *rowptr, const int32_t *cols, const int32_t *wbits,
+                     SparseRegPlan *out);
+
+cudaError_t launch_sparse_reg_sum(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);
+cudaError_t launch_sparse_reg_min(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);
 
 }  // namespace bpg

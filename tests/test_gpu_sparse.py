@@ -27,13 +27,22 @@ def random_pattern(M, max_per_row, rng, integer=False, ebar=40):
             np.array(vals, np.int32 if integer else np.float32))
 
 
-def _run(M, dtype, planes0, unary, pattern, fbar, iters, schedule):
+KERNELS = ["lists", "registers"]
+
+
+def _run(M, dtype, planes0, unary, pattern, fbar, iters, schedule, kernel="auto"):
+    """kernel: "lists", "registers" (the call asserts that it is the one that
+    runs) or "auto"."""
     import torch
     from paper_1010_0012_gb300 import bp
     Hh, W, _ = unary.shape
     G = bp.BPGrid(W, Hh, M, dtype)
     G.set_unary(torch.from_numpy(unary).cuda())
     bp.bp_set_potential_sparse(G.h, *pattern, fbar, dtype)
+    if kernel != "auto":
+        want = bp.BP_SPARSE_LISTS if kernel == "lists" else bp.BP_SPARSE_REGISTERS
+        bp.bp_set_sparse_kernel(G.h, want)
+        assert bp.bp_get_sparse_kernel(G.h)[0] == want
     G.reset()
     if planes0 is not None:
         G.set_messages(torch.from_numpy(planes0).cuda())
@@ -46,9 +55,10 @@ def _run(M, dtype, planes0, unary, pattern, fbar, iters, schedule):
     return out
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("M,k", [(16, 5), (37, 9), (128, 9), (256, 4)])
 @pytest.mark.parametrize("schedule", ["sync", "redblack"])
-def test_sparse_sum_matches_oracle(M, k, schedule):
+def test_sparse_sum_matches_oracle(M, k, schedule, kernel):
     from paper_1010_0012_gb300 import bp
     rng = np.random.default_rng(M + k)
     W, Hh = 11, 7
@@ -56,7 +66,7 @@ def test_sparse_sum_matches_oracle(M, k, schedule):
     pat = random_pattern(M, k, rng)
     fbar = 0.12
     p0 = H.random_planes_sum(W, Hh, M, rng)
-    bel, mp, pl = _run(M, bp.BP_F32, p0, g, pat, fbar, 3, schedule)
+    bel, mp, pl = _run(M, bp.BP_F32, p0, g, pat, fbar, 3, schedule, kernel)
     F = stereo.sparse_compatibility_matrix(*[x.astype(np.float64) if i == 2 else x for i, x in enumerate(pat)],
                                            fbar, M)
     p64, b64 = grid.grid_sum_product(g.astype(np.float64), F, 3, schedule, planes0=p0)
@@ -64,9 +74,10 @@ def test_sparse_sum_matches_oracle(M, k, schedule):
     assert H.message_rel_err(pl, p64, W, Hh) <= H.REL_TOL
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("M,k", [(16, 5), (64, 7), (200, 6)])
 @pytest.mark.parametrize("schedule", ["sync", "redblack"])
-def test_sparse_min_matches_oracle_bit_exact(M, k, schedule):
+def test_sparse_min_matches_oracle_bit_exact(M, k, schedule, kernel):
     from paper_1010_0012_gb300 import bp
     rng = np.random.default_rng(10 * M + k)
     W, Hh = 9, 8
@@ -74,7 +85,7 @@ def test_sparse_min_matches_oracle_bit_exact(M, k, schedule):
     ebar = 40
     pat = random_pattern(M, k, rng, integer=True, ebar=ebar)
     p0 = H.random_planes_min(W, Hh, M, rng)
-    bel, mp, pl = _run(M, bp.BP_I32, p0, E, pat, ebar, 4, schedule)
+    bel, mp, pl = _run(M, bp.BP_I32, p0, E, pat, ebar, 4, schedule, kernel)
     V = stereo.sparse_compatibility_matrix(pat[0], pat[1], pat[2].astype(np.int64), ebar, M, dtype=np.int64)
     p64, b64 = grid.grid_min_sum(E.astype(np.int64), V, 4, schedule, planes0=p0)
     src, dst, side, rr, cc = grid.grid_edges(W, Hh)
@@ -83,7 +94,8 @@ def test_sparse_min_matches_oracle_bit_exact(M, k, schedule):
     np.testing.assert_array_equal(mp, oracle.map_labels(b64, maximise=False))
 
 
-def test_band_written_as_lists_equals_the_band_kernel():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_band_written_as_lists_equals_the_band_kernel(kernel):
     """The truncated potential as a sparse pattern (|x_i - x_j| <= T) gives the
     band kernel's messages (integer: bit for bit)."""
     from paper_1010_0012_gb300 import bp
@@ -98,15 +110,16 @@ def test_band_written_as_lists_equals_the_band_kernel():
                 vals.append(int(tabi[d + cfg.T]))
         rowptr.append(len(cols))
     pat = (np.array(rowptr, np.int32), np.array(cols, np.int32), np.array(vals, np.int32))
-    bel_s, _, pl_s = _run(cfg.M, bp.BP_I32, None, E, pat, ebar, 6, "sync")
+    bel_s, _, pl_s = _run(cfg.M, bp.BP_I32, None, E, pat, ebar, 6, "sync", kernel)
     bel_b, _, pl_b = H.run_gpu_min(E, tabi, cfg.T, ebar, 6, "sync")
     np.testing.assert_array_equal(bel_s, bel_b)
     src, dst, side, rr, cc = grid.grid_edges(cfg.W, cfg.H)
     np.testing.assert_array_equal(pl_s[side, rr, cc], pl_b[side, rr, cc])
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("dtype_name", ["f32", "i32"])
-def test_empty_pattern_leaves_only_the_constant_term(dtype_name):
+def test_empty_pattern_leaves_only_the_constant_term(dtype_name, kernel):
     """No compatible pair at all: every pair has fbar (Ebar), so every
     message is uniform (1/M, or 0 for min-sum), whatever the inputs."""
     from paper_1010_0012_gb300 import bp
@@ -116,7 +129,7 @@ def test_empty_pattern_leaves_only_the_constant_term(dtype_name):
     if dtype_name == "f32":
         g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
         bel, mp, pl = _run(M, bp.BP_F32, None, g, (rowptr, np.zeros(0, np.int32), np.zeros(0, np.float32)),
-                           0.3, 2, "sync")
+                           0.3, 2, "sync", kernel)
         src, dst, side, rr, cc = grid.grid_edges(W, Hh)
         np.testing.assert_allclose(pl[side, rr, cc][:, :M], 1.0 / M, rtol=1e-6)
         b64 = g.astype(np.float64) / g.astype(np.float64).sum(-1, keepdims=True)
@@ -124,7 +137,7 @@ def test_empty_pattern_leaves_only_the_constant_term(dtype_name):
     else:
         E = rng.integers(0, 30, (Hh, W, M)).astype(np.int32)
         bel, mp, pl = _run(M, bp.BP_I32, None, E, (rowptr, np.zeros(0, np.int32), np.zeros(0, np.int32)),
-                           7, 2, "sync")
+                           7, 2, "sync", kernel)
         src, dst, side, rr, cc = grid.grid_edges(W, Hh)
         assert int(np.abs(pl[side, rr, cc][:, :M]).max()) == 0
         np.testing.assert_array_equal(bel.astype(np.int64), E.astype(np.int64))
@@ -182,5 +195,34 @@ def test_sparse_rejects_more_than_512_labels():
     rowptr = np.zeros(601, np.int32)
     with pytest.raises(bp.BPError) as ei:
         bp.bp_set_potential_sparse(G.h, rowptr, np.zeros(0, np.int32), np.zeros(0, np.float32), 0.5, bp.BP_F32)
+    assert ei.value.status == bp.BP_ERR_UNSUPPORTED
+    G.close()
+
+
+def test_kernel_choice_follows_the_pattern():
+    """The register kernel runs by default where the pattern has a schedule;
+    a pattern without one (here M = 300: 512 padded labels) runs on the lists,
+    and asking for registers there is refused."""
+    import torch
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(4)
+    G = bp.BPGrid(5, 4, 128, bp.BP_F32)
+    G.set_unary(torch.ones((4, 5, 128), device="cuda"))
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_get_sparse_kernel(G.h)
+    assert ei.value.status == bp.BP_ERR_STATE
+    pat = random_pattern(128, 9, rng)
+    bp.bp_set_potential_sparse(G.h, *pat, 0.1, bp.BP_F32)
+    kind, steps, wf = bp.bp_get_sparse_kernel(G.h)
+    assert kind == bp.BP_SPARSE_REGISTERS and 9 <= steps <= 12 and wf > 0
+    bp.bp_set_sparse_kernel(G.h, bp.BP_SPARSE_LISTS)
+    assert bp.bp_get_sparse_kernel(G.h) == (bp.BP_SPARSE_LISTS, 0, 0)
+    G.close()
+    G = bp.BPGrid(3, 3, 300, bp.BP_F32)
+    pat = random_pattern(300, 3, rng)
+    bp.bp_set_potential_sparse(G.h, *pat, 0.1, bp.BP_F32)
+    assert bp.bp_get_sparse_kernel(G.h)[0] == bp.BP_SPARSE_LISTS
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_set_sparse_kernel(G.h, bp.BP_SPARSE_REGISTERS)
     assert ei.value.status == bp.BP_ERR_UNSUPPORTED
     G.close()
