@@ -681,11 +681,11 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
     BP_CK(h, cudaMemcpyAsync(h->d_sp_len, len.data(), (size_t)h->M * 4, cudaMemcpyHostToDevice, h->stream));
     BP_CK(h, cudaMemcpyAsync(h->d_sp_ell, ell.data(), ell.size() * 4, cudaMemcpyHostToDevice, h->stream));
     if (reg_ok) {
-        if (bp_status st = ensure_buffer(h, &h->d_sp_rent, plan.ent.size() * 4, "register pattern")) return st;
+        const std::vector<int32_t> dent = sparse_reg_device_entries(plan, h->dtype == BP_I32);
+        if (bp_status st = ensure_buffer(h, &h->d_sp_rent, dent.size() * 4, "register pattern")) return st;
         if (bp_status st = ensure_buffer(h, &h->d_sp_rlab, plan.lab.size() * 4, "register pattern labels"))
             return st;
-        BP_CK(h, cudaMemcpyAsync(h->d_sp_rent, plan.ent.data(), plan.ent.size() * 4, cudaMemcpyHostToDevice,
-                                 h->stream));
+        BP_CK(h, cudaMemcpyAsync(h->d_sp_rent, dent.data(), dent.size() * 4, cudaMemcpyHostToDevice, h->stream));
         BP_CK(h, cudaMemcpyAsync(h->d_sp_rlab, plan.lab.data(), plan.lab.size() * 4, cudaMemcpyHostToDevice,
                                  h->stream));
         h->sp_reg = true;

@@ -46,6 +46,11 @@ cudaError_t launch_sparse_min(const SparseArgsI &a, cudaStream_t s);
 // Lane l of 32-label receiver block k owns the receiver label lab[k][l] (-1:
 // none) and, for each step c < LM, the entry ent[k][c][l] = (byte offset of
 // the sender label's h slot, or 0xFFFF for a hole; bits of f - fbar, or E).
+// The device copy of a schedule has no holes: a hole reads slot 0 (label 0,
+// always a label) with the value 0.0f (sum: adds nothing) or kSparseHoleE
+// (min-sum: E + h never goes below Ebar + min h, the flat term).
+constexpr int32_t kSparseHoleE = 1 << 29;
+
 struct SparseRegArgs {
     const void *u;           // [H][W][Mp] g (float) or E_u (int32)
     const void *in;          // [4][H][W][Mp] incoming messages
@@ -61,21 +66,28 @@ struct SparseRegArgs {
 
 // (KM, LM) pairs compiled: KM = 32-label receiver blocks (Mp <= 32 KM), LM =
 // register steps per block; LM ascending for each KM.
-constexpr int kSparseRegVariants[][2] = {{1, 16}, {1, 48}, {2, 12}, {2, 24}, {4, 6}, {4, 12}, {8, 6}};
+constexpr int kSparseRegVariants[][2] = {{1, 16}, {1, 48}, {2, 8}, {2, 12}, {2, 24}, {4, 6},
+                                          {4, 9},  {4, 12}, {8, 4}, {8, 6}};
 
 struct SparseRegPlan {
     int KM = 0, LM = 0;
-    int steps = 0;                 // largest quarter-warp schedule (LM >= steps)
-    int wavefronts = 0;            // sum over quarter-warps of their steps: gather wavefronts per node
+    int steps = 0;                 // steps every lane runs per block (= LM)
+    int wavefronts = 0;            // gather wavefronts per node (sum over blocks, quarter-warps, steps)
     std::vector<int32_t> ent;      // [KM][LM][32][2]
     std::vector<int32_t> lab;      // [KM][32]
 };
 
 // Schedules a pattern (CSR by receiver label; wbits = value bits per entry)
-// for the register kernels.  False when Mp > 256 or when the schedule needs
-// more steps than any compiled variant holds (the list kernels serve it).
+// for the register kernels; holes have offset 0xFFFF.  False when Mp > 256
+// or when a list is longer than the steps of every compiled variant (the list
+// kernels serve it).
 bool sparse_reg_plan(int M, int Mp, const int32_t *rowptr, const int32_t *cols, const int32_t *wbits,
                      SparseRegPlan *out);
+
+// The entries as the kernel takes them: a hole reads a slot that another lane
+// of its quarter-warp reads at that step (no extra wavefront), or slot 0, with
+// a value that changes nothing.
+std::vector<int32_t> sparse_reg_device_entries(const SparseRegPlan &plan, bool min_sum);
 
 cudaError_t launch_sparse_reg_sum(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);
 cudaError_t launch_sparse_reg_min(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);

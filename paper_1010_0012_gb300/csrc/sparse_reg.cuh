@@ -39,7 +39,6 @@ namespace sr {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr uint32_t kHole = 0xFFFFu;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int32_t kBigE = 1 << 30;
 
@@ -56,8 +55,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 }
 
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
@@ -189,10 +186,8 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
 
     const int nslots = a.parity < 0 ? W * H : ((W + 1) >> 1) * H;
     const int nw = gridDim.x * kWarps;
-    auto issue = [&](int s, int st) {   // lane 0: the node's unary and incoming vectors into stage st
-        int r = 0, c = 0;
-        slot_node(s, nslots, W, a.parity, r, c);
-        const long long o = ((long long)r * W + c) * Mp;
+    auto issue = [&](int rr, int cc, int st) {   // lane 0: node (rr, cc)'s unary and incoming vectors into stage st
+        const long long o = ((long long)rr * W + cc) * Mp;
         mbar_expect_tx(&bar[st], 5 * vbytes);
         bulk_g2s(stage[st], (const T *)a.u + o, vbytes, &bar[st]);
 #pragma unroll
@@ -200,21 +195,25 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
     };
 
     int cur = next_slot(blockIdx.x * kWarps + warp, nslots, nw, W, a.parity);
+    int r = 0, c = 0;
+    slot_node(cur, nslots, W, a.parity, r, c);
     uint32_t ph = 0, pending = 0;
     int st = 0;
     if (cur < nslots) {
-        if (lane == 0) issue(cur, 0);
+        if (lane == 0) issue(r, c, 0);
         pending = 1;
     }
     bool ok = true;
     while (cur < nslots) {
         const int nxt = next_slot(cur + nw, nslots, nw, W, a.parity);
+        int rn = 0, cn = 0;
+        slot_node(nxt, nslots, W, a.parity, rn, cn);
         if (nxt < nslots) {
-            // stage st ^ 1 was read by the previous node's phase 1: order those
-            // reads before the copies that overwrite it
-            fence_proxy_async();
+            // stage st ^ 1 was read by the previous node's phase 1; those reads
+            // have returned (their values were consumed) and the warp has
+            // synchronised since, so the copies may overwrite it
             __syncwarp();
-            if (lane == 0) issue(nxt, st ^ 1);
+            if (lane == 0) issue(rn, cn, st ^ 1);
             pending |= 1u << (st ^ 1);
         }
         ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], (ph >> st) & 1u));
@@ -222,8 +221,6 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
         ph ^= 1u << st;
         pending &= ~(1u << st);
 
-        int r = 0, c = 0;
-        slot_node(cur, nslots, W, a.parity, r, c);
         const bool has[4] = {c > 0, c < W - 1, r > 0, r < H - 1};
         const T *sg = stage[st];
 
@@ -267,14 +264,14 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
             }
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+        for (int t = 0; t < 4; ++t) {
+            if constexpr (MIN) {
+                S[t] = __reduce_min_sync(0xffffffffu, S[t]);
+            } else {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                if constexpr (MIN)
-                    S[t] = min(S[t], __shfl_xor_sync(0xffffffffu, S[t], o));
-                else
-                    S[t] += __shfl_xor_sync(0xffffffffu, S[t], o);
+                for (int o = 16; o > 0; o >>= 1) S[t] += __shfl_xor_sync(0xffffffffu, S[t], o);
             }
+        }
         __syncwarp();
 
         // phase 2: the band of every receiver label this lane owns, from the
@@ -293,8 +290,11 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
                 const int i = k * LM + c2;
+                // a hole reads slot 0 with a value that changes nothing (0 in
+                // a sum, 2^29 in a minimum): no branch, so the gathers can be
+                // issued ahead of their use
                 const uint32_t off = (so[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
-                if (off != kHole) {
+                {
                     const V hv = *(const V *)(hb + off);
                     if constexpr (MIN) {
                         u[k].x = __viaddmin_s32(wv[i], hv.x, u[k].x);
@@ -338,14 +338,14 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
             }
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+        for (int t = 0; t < 4; ++t) {
+            if constexpr (MIN) {
+                Z[t] = __reduce_min_sync(0xffffffffu, Z[t]);
+            } else {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                if constexpr (MIN)
-                    Z[t] = min(Z[t], __shfl_xor_sync(0xffffffffu, Z[t], o));
-                else
-                    Z[t] += __shfl_xor_sync(0xffffffffu, Z[t], o);
+                for (int o = 16; o > 0; o >>= 1) Z[t] += __shfl_xor_sync(0xffffffffu, Z[t], o);
             }
+        }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (!has[t]) continue;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
                     if (lk != 0xFFFF) dst[lk] = lk < M ? comp(u[k], t) - Z[t] : 0;
                 }
             } else {
-                const float inv = 1.f / Z[t];
+                const float inv = __frcp_rn(Z[t]);   // the correctly rounded 1 / Z
 #pragma unroll
                 for (int k = 0; k < KM; ++k) {
                     const int lk = (labp[k >> 1] >> ((k & 1) * 16)) & 0xFFFF;
@@ -368,6 +368,8 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
         __syncwarp();   // the h slice is rewritten by the warp's next node
         st ^= 1;
         cur = nxt;
+        r = rn;
+        c = cn;
     }
     if (!ok) {
         if (lane == 0) atomicExch(a.status, 301);

@@ -6,21 +6,18 @@
 // 32-label block can be given to the block's 32 lanes in any order (a store is
 // still one 128-byte line).  Both freedoms go into shared-memory bank
 // conflicts.  A 16-byte gather by the eight lanes of a quarter-warp costs one
-// wavefront per distinct slot in the most-used 16-byte bank group.  Label x
-// lives in slot (x & ~31) | ((x & 3) << 3) | ((x >> 2) & 7), bank group
-// (x >> 2) & 7.
+// wavefront per distinct slot in its most-used 16-byte bank group (lanes that
+// read the same slot share it).  Label x lives in slot
+// (x & ~31) | ((x & 3) << 3) | ((x >> 2) & 7), bank group (x >> 2) & 7.
 //
 // 1. Partition: each block's labels are split into four quarter-warps of
 //    eight so that every quarter-warp's entries spread evenly over the eight
-//    bank groups.  A quarter-warp whose most-used group holds N entries needs
-//    at least max(N, longest list) gathers.  The split minimises the sum and
-//    the maximum of that bound by deterministic annealing over swaps.
-// 2. Schedule: within a quarter-warp the entries form a bipartite multigraph,
-//    lanes against bank groups.  A proper edge colouring with D colours, D its
-//    largest degree, exists (Koenig's theorem).  It is found by the classical
-//    alternating-path recolouring.  Colour c is step c: at every step each lane
-//    takes at most one entry and each bank group serves at most one lane, one
-//    wavefront.  Lanes whose list is shorter than D have holes.
+//    bank groups (deterministic annealing over swaps of two labels).
+// 2. Steps: the kernel runs LM steps per block, LM the smallest compiled step
+//    count at least the longest list.  Each lane places its entries on
+//    distinct steps (holes elsewhere); the placement minimises the sum over
+//    steps of the step's wavefronts, again by deterministic annealing over
+//    swaps of two steps of one lane.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -45,57 +42,6 @@ struct XorShift {
     double unit() { return (next() & 0xFFFFFF) / 16777216.0; }
 };
 
-// Edge colouring of a bipartite multigraph with lanes 0..7 on one side and
-// bank groups 0..7 on the other; edge e joins lane el[e] and group eg[e].
-// Returns the number of colours (the largest degree); col[e] is e's colour.
-int colour_edges(const std::vector<int> &el, const std::vector<int> &eg, std::vector<int> &col) {
-    const int E = (int)el.size();
-    int degL[8] = {}, degG[8] = {};
-    for (int e = 0; e < E; ++e) {
-        ++degL[el[e]];
-        ++degG[eg[e]];
-    }
-    int D = 0;
-    for (int i = 0; i < 8; ++i) D = std::max(D, std::max(degL[i], degG[i]));
-    col.assign(E, -1);
-    if (D == 0) return 0;
-    std::vector<int> atL(8 * D, -1), atG(8 * D, -1);   // edge holding colour c at a vertex
-    for (int e = 0; e < E; ++e) {
-        const int p = el[e], g = eg[e];
-        int a = 0, b = 0;
-        while (atL[p * D + a] >= 0) ++a;   // free at the lane (degree < D before e)
-        while (atG[g * D + b] >= 0) ++b;   // free at the group
-        if (atG[g * D + a] >= 0) {
-            // the path from g alternating colours a, b never reaches p (a is
-            // free at p); swapping a and b along it frees a at g
-            std::vector<int> path;
-            bool at_group = true;
-            int v = g, c = a;
-            for (;;) {
-                const int f = at_group ? atG[v * D + c] : atL[v * D + c];
-                if (f < 0) break;
-                path.push_back(f);
-                v = at_group ? el[f] : eg[f];
-                at_group = !at_group;
-                c = (c == a) ? b : a;
-            }
-            for (int f : path) {
-                atL[el[f] * D + col[f]] = -1;
-                atG[eg[f] * D + col[f]] = -1;
-            }
-            for (int f : path) {
-                col[f] = (col[f] == a) ? b : a;
-                atL[el[f] * D + col[f]] = f;
-                atG[eg[f] * D + col[f]] = f;
-            }
-        }
-        col[e] = a;
-        atL[p * D + a] = e;
-        atG[g * D + a] = e;
-    }
-    return D;
-}
-
 struct QuarterCost {
     int bound;      // max(largest group count, longest list)
     long long sq;   // sum of squared group counts (a tie-break toward even spreads)
@@ -117,16 +63,122 @@ QuarterCost quarter_cost(const std::vector<int> &pos, int q, int n, const std::v
     return c;
 }
 
-// weight of one partition: the sum and the maximum of the quarter-warp bounds
-// first (wavefronts and register steps), then the spread
 long long partition_weight(const QuarterCost *qc, int nq) {
-    long long sum = 0, mx = 0, sq = 0;
+    long long sum = 0, sq = 0;
     for (int q = 0; q < nq; ++q) {
         sum += qc[q].bound;
-        mx = std::max<long long>(mx, qc[q].bound);
         sq += qc[q].sq;
     }
-    return ((2 * sum + mx) << 20) + sq;
+    return (sum << 20) + sq;
+}
+
+// Split the n labels pos[] of one block into quarter-warps (positions 8q ..
+// 8q + 7) with evenly spread bank groups.
+void partition_block(std::vector<int> &pos, const std::vector<int> &len, const std::vector<int> &hist,
+                     XorShift &rng) {
+    const int n = (int)pos.size(), nq = (n + 7) / 8;
+    std::stable_sort(pos.begin(), pos.end(), [&](int x, int y) { return len[x] > len[y]; });
+    std::vector<int> dealt(n);
+    int fill[4] = {0, 0, 0, 0}, q = 0;
+    for (int i = 0; i < n; ++i) {   // longest lists first, round robin over the quarters
+        while (fill[q] >= std::min(8, n - 8 * q)) q = (q + 1) % nq;
+        dealt[8 * q + fill[q]++] = pos[i];
+        q = (q + 1) % nq;
+    }
+    pos = dealt;
+    if (nq < 2) return;
+    QuarterCost qc[4];
+    for (int j = 0; j < nq; ++j) qc[j] = quarter_cost(pos, j, n, len, hist);
+    long long cur = partition_weight(qc, nq), best = cur;
+    std::vector<int> best_pos = pos;
+    double temp = 2.0 * (1 << 20);
+    for (int it = 0; it < 6000; ++it) {
+        const int qa = (int)(rng.next() % nq);
+        int qb = (int)(rng.next() % (nq - 1));
+        if (qb >= qa) ++qb;
+        const int ia = 8 * qa + (int)(rng.next() % std::min(8, n - 8 * qa));
+        const int ib = 8 * qb + (int)(rng.next() % std::min(8, n - 8 * qb));
+        std::swap(pos[ia], pos[ib]);
+        const QuarterCost ca = qc[qa], cb = qc[qb];
+        qc[qa] = quarter_cost(pos, qa, n, len, hist);
+        qc[qb] = quarter_cost(pos, qb, n, len, hist);
+        const long long w = partition_weight(qc, nq);
+        if (w <= cur || rng.unit() < std::exp((double)(cur - w) / temp)) {
+            cur = w;
+            if (cur < best) {
+                best = cur;
+                best_pos = pos;
+            }
+        } else {
+            std::swap(pos[ia], pos[ib]);
+            qc[qa] = ca;
+            qc[qb] = cb;
+        }
+        temp = std::max(1.0, temp * 0.9985);
+    }
+    pos = best_pos;
+}
+
+// Wavefronts of one step of one quarter-warp: distinct slots in its most-used
+// bank group (at least one: hole lanes still issue the gather).
+int step_cost(const std::vector<int> &sched, int nl, int LM, int c) {
+    int slots[8], groups[8], m = 0;
+    for (int l = 0; l < nl; ++l) {
+        const int x = sched[l * LM + c];
+        if (x < 0) continue;
+        const int s = reg_slot(x);
+        bool dup = false;
+        for (int j = 0; j < m; ++j) dup = dup || slots[j] == s;
+        if (!dup) {
+            slots[m] = s;
+            groups[m++] = reg_group(x);
+        }
+    }
+    int cnt[8] = {}, best = 1;
+    for (int j = 0; j < m; ++j) best = std::max(best, ++cnt[groups[j]]);
+    return best;
+}
+
+// Place the entries (sender labels) of each lane of one quarter-warp on
+// distinct steps 0..LM-1; sched[l * LM + c] = sender label or -1 (hole).
+// Returns the quarter-warp's wavefronts per node.
+int place_quarter(std::vector<int> &sched, const std::vector<std::vector<int>> &lists, int LM, XorShift &rng) {
+    const int nl = (int)lists.size();
+    sched.assign((size_t)nl * LM, -1);
+    for (int l = 0; l < nl; ++l)
+        for (size_t i = 0; i < lists[l].size(); ++i) sched[l * LM + (int)i] = lists[l][i];
+    std::vector<int> cost(LM);
+    int cur = 0;
+    for (int c = 0; c < LM; ++c) cur += (cost[c] = step_cost(sched, nl, LM, c));
+    if (nl == 0 || LM < 2) return cur;
+    int best = cur;
+    std::vector<int> best_sched = sched;
+    double temp = 1.0;
+    const int iters = 2500 * nl;
+    for (int it = 0; it < iters && best > LM; ++it) {
+        const int l = (int)(rng.next() % nl);
+        const int a = (int)(rng.next() % LM);
+        int b = (int)(rng.next() % (LM - 1));
+        if (b >= a) ++b;
+        if (sched[l * LM + a] < 0 && sched[l * LM + b] < 0) continue;
+        std::swap(sched[l * LM + a], sched[l * LM + b]);
+        const int ca = step_cost(sched, nl, LM, a), cb = step_cost(sched, nl, LM, b);
+        const int next = cur - cost[a] - cost[b] + ca + cb;
+        if (next <= cur || rng.unit() < std::exp((double)(cur - next) / temp)) {
+            cur = next;
+            cost[a] = ca;
+            cost[b] = cb;
+            if (cur < best) {
+                best = cur;
+                best_sched = sched;
+            }
+        } else {
+            std::swap(sched[l * LM + a], sched[l * LM + b]);
+        }
+        temp = std::max(0.02, temp * 0.9997);
+    }
+    sched = best_sched;
+    return best;
 }
 
 }  // namespace
@@ -135,115 +187,82 @@ bool sparse_reg_plan(int M, int Mp, const int32_t *rowptr, const int32_t *cols, 
                      SparseRegPlan *out) {
     if (Mp > 256 || Mp < 4) return false;
     const int KM = Mp <= 32 ? 1 : Mp / 32;
-    int LMcap = 0;
-    for (const auto &v : kSparseRegVariants)
-        if (v[0] == KM) LMcap = std::max(LMcap, v[1]);
-    if (LMcap == 0) return false;
     std::vector<int> len(Mp, 0), hist((size_t)Mp * 8, 0);
+    int lmax = 0;
     for (int x = 0; x < M; ++x) {
         len[x] = rowptr[x + 1] - rowptr[x];
-        if (len[x] > LMcap) return false;
+        lmax = std::max(lmax, len[x]);
         for (int p = rowptr[x]; p < rowptr[x + 1]; ++p) ++hist[(size_t)x * 8 + reg_group(cols[p])];
-    }
-    // ent[k][c][lane] with c < LMcap first; compacted to the chosen LM below
-    std::vector<int32_t> ent((size_t)KM * LMcap * 32 * 2, 0);
-    for (size_t i = 0; i < ent.size(); i += 2) ent[i] = (int32_t)0xFFFF;
-    std::vector<int32_t> lab((size_t)KM * 32, -1);
-    int steps = 0, wavefronts = 0;
-    XorShift rng{0x9E3779B97F4A7C15ull};
-    for (int k = 0; k < KM; ++k) {
-        const int base = 32 * k, n = std::min(32, Mp - base);
-        const int nq = (n + 7) / 8;
-        std::vector<int> pos(n);
-        for (int i = 0; i < n; ++i) pos[i] = base + i;
-        // start from the labels dealt longest list first, round robin over the quarters
-        std::stable_sort(pos.begin(), pos.end(), [&](int x, int y) { return len[x] > len[y]; });
-        std::vector<int> dealt(n);
-        {
-            int fill[4] = {0, 0, 0, 0}, q = 0;
-            for (int i = 0; i < n; ++i) {
-                while (fill[q] >= std::min(8, n - 8 * q)) q = (q + 1) % nq;
-                dealt[8 * q + fill[q]++] = pos[i];
-                q = (q + 1) % nq;
-            }
-        }
-        pos = dealt;
-        QuarterCost qc[4];
-        for (int q = 0; q < nq; ++q) qc[q] = quarter_cost(pos, q, n, len, hist);
-        if (nq > 1) {
-            long long cur = partition_weight(qc, nq), best = cur;
-            std::vector<int> best_pos = pos;
-            double temp = 2.0 * (1 << 20);
-            const int iters = 6000;
-            for (int it = 0; it < iters; ++it) {
-                const int qa = (int)(rng.next() % nq);
-                int qb = (int)(rng.next() % (nq - 1));
-                if (qb >= qa) ++qb;
-                const int na = std::min(8, n - 8 * qa), nb = std::min(8, n - 8 * qb);
-                const int ia = 8 * qa + (int)(rng.next() % na), ib = 8 * qb + (int)(rng.next() % nb);
-                std::swap(pos[ia], pos[ib]);
-                const QuarterCost ca = qc[qa], cb = qc[qb];
-                qc[qa] = quarter_cost(pos, qa, n, len, hist);
-                qc[qb] = quarter_cost(pos, qb, n, len, hist);
-                const long long w = partition_weight(qc, nq);
-                if (w <= cur || rng.unit() < std::exp((double)(cur - w) / temp)) {
-                    cur = w;
-                    if (cur < best) {
-                        best = cur;
-                        best_pos = pos;
-                    }
-                } else {
-                    std::swap(pos[ia], pos[ib]);
-                    qc[qa] = ca;
-                    qc[qb] = cb;
-                }
-                temp = std::max(1.0, temp * 0.9985);
-            }
-            pos = best_pos;
-        }
-        for (int i = 0; i < n; ++i) lab[(size_t)k * 32 + i] = pos[i];
-        for (int q = 0; q < nq; ++q) {
-            std::vector<int> el, eg, idx;
-            for (int i = 8 * q; i < std::min(n, 8 * q + 8); ++i) {
-                const int x = pos[i];
-                if (x >= M) continue;
-                for (int p = rowptr[x]; p < rowptr[x + 1]; ++p) {
-                    el.push_back(i - 8 * q);
-                    eg.push_back(reg_group(cols[p]));
-                    idx.push_back(p);
-                }
-            }
-            std::vector<int> col;
-            const int D = colour_edges(el, eg, col);
-            if (D > LMcap) return false;
-            steps = std::max(steps, D);
-            wavefronts += D;
-            for (size_t e = 0; e < idx.size(); ++e) {
-                const int lane = 8 * q + el[e];
-                const size_t o = (((size_t)k * LMcap + col[e]) * 32 + lane) * 2;
-                ent[o] = reg_slot(cols[idx[e]]) * 16;
-                ent[o + 1] = wbits[idx[e]];
-            }
-        }
     }
     int LM = 0;
     for (const auto &v : kSparseRegVariants)
-        if (v[0] == KM && v[1] >= steps && LM == 0) LM = v[1];
+        if (v[0] == KM && v[1] >= lmax && LM == 0) LM = v[1];
     if (LM == 0) return false;
     out->KM = KM;
     out->LM = LM;
-    out->steps = steps;
-    out->wavefronts = wavefronts;
-    out->lab = lab;
+    out->steps = LM;
+    out->lab.assign((size_t)KM * 32, -1);
     out->ent.assign((size_t)KM * LM * 32 * 2, 0);
-    for (int k = 0; k < KM; ++k)
-        for (int c = 0; c < LM; ++c)
-            for (int l = 0; l < 32; ++l) {
-                const size_t d = (((size_t)k * LM + c) * 32 + l) * 2, s = (((size_t)k * LMcap + c) * 32 + l) * 2;
-                out->ent[d] = ent[s];
-                out->ent[d + 1] = ent[s + 1];
+    for (size_t i = 0; i < out->ent.size(); i += 2) out->ent[i] = 0xFFFF;
+    int wavefronts = 0;
+    XorShift rng{0x9E3779B97F4A7C15ull};
+    for (int k = 0; k < KM; ++k) {
+        const int base = 32 * k, n = std::min(32, Mp - base);
+        std::vector<int> pos(n);
+        for (int i = 0; i < n; ++i) pos[i] = base + i;
+        partition_block(pos, len, hist, rng);
+        for (int i = 0; i < n; ++i) out->lab[(size_t)k * 32 + i] = pos[i];
+        for (int q = 0; q < 4; ++q) {
+            std::vector<std::vector<int>> lists, where;   // sender labels / CSR positions per lane
+            for (int i = 8 * q; i < std::min(n, 8 * q + 8); ++i) {
+                lists.emplace_back();
+                where.emplace_back();
+                const int x = pos[i];
+                if (x >= M) continue;
+                for (int p = rowptr[x]; p < rowptr[x + 1]; ++p) {
+                    lists.back().push_back(cols[p]);
+                    where.back().push_back(p);
+                }
             }
+            std::vector<int> sched;
+            wavefronts += place_quarter(sched, lists, LM, rng);
+            for (int l = 0; l < (int)lists.size(); ++l)
+                for (int c = 0; c < LM; ++c) {
+                    const int xi = sched[l * LM + c];
+                    if (xi < 0) continue;
+                    // the CSR position of this sender label in the lane's row
+                    int p = -1;
+                    for (size_t j = 0; j < lists[l].size(); ++j)
+                        if (lists[l][j] == xi) p = where[l][j];
+                    const size_t o = (((size_t)k * LM + c) * 32 + 8 * q + l) * 2;
+                    out->ent[o] = reg_slot(xi) * 16;
+                    out->ent[o + 1] = wbits[p];
+                }
+        }
+    }
+    out->wavefronts = wavefronts;
     return true;
+}
+
+std::vector<int32_t> sparse_reg_device_entries(const SparseRegPlan &plan, bool min_sum) {
+    std::vector<int32_t> ent = plan.ent;
+    for (int k = 0; k < plan.KM; ++k)
+        for (int c = 0; c < plan.LM; ++c)
+            for (int q = 0; q < 4; ++q) {
+                const size_t b = (((size_t)k * plan.LM + c) * 32 + 8 * q) * 2;
+                int32_t share = 0;   // a slot another lane of the quarter reads at this step
+                for (int l = 0; l < 8; ++l)
+                    if (ent[b + 2 * l] != 0xFFFF) {
+                        share = ent[b + 2 * l];
+                        break;
+                    }
+                for (int l = 0; l < 8; ++l)
+                    if (ent[b + 2 * l] == 0xFFFF) {
+                        ent[b + 2 * l] = share;
+                        ent[b + 2 * l + 1] = min_sum ? kSparseHoleE : 0;   // 0: the bits of 0.0f
+                    }
+            }
+    return ent;
 }
 
 }  // namespace bpg
