@@ -37,8 +37,8 @@
 namespace bpg {
 namespace sr {
 
-constexpr int kBlock = 256;
-constexpr int kWarps = kBlock / 32;
+constexpr int kBlock = 32;             // one warp per block: every shared address is a block constant
+constexpr int kMinBlocks = 16;         // resident blocks per SM the registers must allow (128 each)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 constexpr int32_t kBigE = 1 << 30;
 
@@ -89,25 +89,43 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-// slot -> node of a synchronous iteration (parity < 0) or of a red-black half-step
-__device__ __forceinline__ bool slot_node(int slot, int nslots, int W, int parity, int &r, int &c) {
-    if (slot >= nslots) return false;
-    if (parity < 0) {
-        r = slot / W;
-        c = slot - r * W;
-        return true;
+// Walks the nodes of a launch with a stride of `nw` slots.  Slots are the
+// nodes in row-major order (synchronous iteration, parity < 0), or of a
+// red-black half-step the row-major slots ch of the nodes with
+// (r + c) % 2 == parity, c = 2 ch + ((r + parity) & 1).  A step adds the
+// stride without a division.
+struct NodeWalk {
+    int r, ch, dq, dr, row, W, H, parity;
+    __device__ __forceinline__ void init(int slot, int nw, int W_, int H_, int parity_) {
+        W = W_;
+        H = H_;
+        parity = parity_;
+        row = parity < 0 ? W : (W + 1) >> 1;
+        r = slot / row;
+        ch = slot - r * row;
+        dq = nw / row;
+        dr = nw - dq * row;
+        settle();
     }
-    const int Wh = (W + 1) >> 1;
-    r = slot / Wh;
-    c = 2 * (slot - r * Wh) + ((r + parity) & 1);
-    return c < W;
-}
-
-__device__ __forceinline__ int next_slot(int s, int nslots, int nw, int W, int parity) {
-    int r, c;
-    while (s < nslots && !slot_node(s, nslots, W, parity, r, c)) s += nw;
-    return s;
-}
+    __device__ __forceinline__ int col() const { return parity < 0 ? ch : 2 * ch + ((r + parity) & 1); }
+    __device__ __forceinline__ bool live() const { return r < H; }
+    __device__ __forceinline__ void step() {
+        ch += dr;
+        r += dq;
+        if (ch >= row) {
+            ch -= row;
+            ++r;
+        }
+    }
+    // the last slot of a row of odd width has no node of one parity
+    __device__ __forceinline__ void settle() {
+        while (r < H && col() >= W) step();
+    }
+    __device__ __forceinline__ void next() {
+        step();
+        settle();
+    }
+};
 
 __device__ __forceinline__ long long dst_offset(int t, int r, int c, int W, long long plane, int Mp) {
     const int dr = (t == 2) ? -1 : (t == 3) ? 1 : 0;
@@ -138,25 +156,95 @@ __host__ __device__ inline size_t warp_smem_bytes(int Mp) {
     return (size_t)2 * 5 * Mp * 4 + (size_t)hslots * 16 + 16;
 }
 
+// Sum of four values over the warp, returned to every lane: two exchange
+// rounds leave each lane one direction's partial (bits 4 and 3 of the lane),
+// three more rounds finish it, four reads broadcast the totals.
+__device__ __forceinline__ void warp_sum4(float (&v)[4], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8;
+    float k0 = b4 ? v[2] : v[0], k1 = b4 ? v[3] : v[1];
+    k0 += __shfl_xor_sync(0xffffffffu, b4 ? v[0] : v[2], 16);
+    k1 += __shfl_xor_sync(0xffffffffu, b4 ? v[1] : v[3], 16);
+    float k = b3 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, b3 ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    v[0] = __shfl_sync(0xffffffffu, k, 0);
+    v[1] = __shfl_sync(0xffffffffu, k, 8);
+    v[2] = __shfl_sync(0xffffffffu, k, 16);
+    v[3] = __shfl_sync(0xffffffffu, k, 24);
+}
+
+// Phase 1 for one node: h of the four directions per label (Eq. 5) from the
+// staged unary and incoming vectors into the h slice, and the outer terms S
+// (sum of h, or its minimum) per direction, this lane's part.  FAST: every
+// neighbour present and M == Mp (no masks, no selects).
+template <bool MIN, bool FAST>
+__device__ __forceinline__ void form_h(const typename Types<MIN>::T *sg, typename Types<MIN>::V *h4, int M, int Mp,
+                                       int lane, const bool (&has)[4], typename Types<MIN>::T (&S)[4]) {
+    using T = typename Types<MIN>::T;
+    using V = typename Types<MIN>::V;
+    for (int x0 = 4 * lane; x0 < Mp; x0 += 128) {
+        const V gv = *(const V *)(sg + x0);
+        V m[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const V in = *(const V *)(sg + (1 + t) * Mp + x0);
+            if constexpr (FAST) {
+                m[t] = in;
+            } else {
+                if constexpr (MIN)
+                    m[t] = has[t] ? in : make_int4(0, 0, 0, 0);
+                else
+                    m[t] = has[t] ? in : make_float4(1.f, 1.f, 1.f, 1.f);
+            }
+        }
+        const int sbase = (x0 & ~31) | (lane & 7);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const T m0 = comp(m[0], j), m1 = comp(m[1], j), m2 = comp(m[2], j), m3 = comp(m[3], j);
+            V hv;
+            if constexpr (MIN) {
+                // padded labels (never a pattern column) stay out of the minima
+                const int32_t tot = (FAST || x0 + j < M) ? comp(gv, j) + m0 + m1 + m2 + m3 : kBigE;
+                hv = make_int4(tot - m0, tot - m1, tot - m2, tot - m3);
+                S[0] = min(S[0], hv.x);
+                S[1] = min(S[1], hv.y);
+                S[2] = min(S[2], hv.z);
+                S[3] = min(S[3], hv.w);
+            } else {
+                const float g = (FAST || x0 + j < M) ? comp(gv, j) : 0.f;
+                const float g01 = g * m0 * m1, g23 = g * m2 * m3;
+                hv = make_float4(g23 * m1, g23 * m0, g01 * m3, g01 * m2);
+                S[0] += hv.x;
+                S[1] += hv.y;
+                S[2] += hv.z;
+                S[3] += hv.w;
+            }
+            h4[sbase + (j << 3)] = hv;
+        }
+    }
+}
+
 template <int KM, int LM, bool MIN>
-__global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegArgs a) {
+__global__ void __launch_bounds__(kBlock, kMinBlocks) sparse_reg_kernel(const SparseRegArgs a) {
     using T = typename Types<MIN>::T;
     using V = typename Types<MIN>::V;
     extern __shared__ __align__(128) unsigned char sr_raw[];
     const int M = a.d.M, Mp = a.d.Mp, W = a.d.W, H = a.d.H;
     const long long plane = a.d.plane;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x;
     const int hslots = Mp < 32 ? 32 : Mp;
     const uint32_t vbytes = (uint32_t)Mp * 4;
-    unsigned char *wb = sr_raw + (size_t)warp * warp_smem_bytes(Mp);
-    T *stage[2] = {(T *)wb, (T *)wb + 5 * Mp};
-    V *h4 = (V *)(wb + (size_t)10 * vbytes);
-    uint64_t *bar = (uint64_t *)(wb + (size_t)10 * vbytes + (size_t)hslots * 16);
+    T *stage[2] = {(T *)sr_raw, (T *)sr_raw + 5 * Mp};
+    V *h4 = (V *)(sr_raw + (size_t)10 * vbytes);
+    uint64_t *bar = (uint64_t *)(sr_raw + (size_t)10 * vbytes + (size_t)hslots * 16);
 
     // this lane's share of the pattern, once per launch
     T wv[KM * LM];
     uint32_t so[(KM * LM + 1) / 2];
     uint32_t labp[(KM + 1) / 2];   // receiver label of block k in half k % 2 of word k / 2; 0xFFFF: none
+    uint32_t real = 0;             // bit k: the label of block k is a label (< M)
 #pragma unroll
     for (int i = 0; i < (KM * LM + 1) / 2; ++i) so[i] = 0;
 #pragma unroll
@@ -165,6 +253,7 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
     for (int k = 0; k < KM; ++k) {
         const int lk = a.lab[k * 32 + lane];
         labp[k >> 1] |= (uint32_t)(lk < 0 ? 0xFFFF : lk) << ((k & 1) * 16);
+        if (lk >= 0 && lk < M) real |= 1u << k;
 #pragma unroll
         for (int c = 0; c < LM; ++c) {
             const int i = k * LM + c;
@@ -176,6 +265,7 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
             so[i >> 1] |= ((uint32_t)e.x & 0xFFFFu) << ((i & 1) * 16);
         }
     }
+    const bool all_lanes_labelled = Mp >= 32;   // else some lanes own no label
 
     if (lane == 0) {
         mbar_init(&bar[0], 1);
@@ -184,9 +274,8 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
     }
     __syncwarp();
 
-    const int nslots = a.parity < 0 ? W * H : ((W + 1) >> 1) * H;
-    const int nw = gridDim.x * kWarps;
-    auto issue = [&](int rr, int cc, int st) {   // lane 0: node (rr, cc)'s unary and incoming vectors into stage st
+    // lane 0: node (rr, cc)'s unary and incoming vectors into stage st
+    auto issue = [&](int rr, int cc, int st) {
         const long long o = ((long long)rr * W + cc) * Mp;
         mbar_expect_tx(&bar[st], 5 * vbytes);
         bulk_g2s(stage[st], (const T *)a.u + o, vbytes, &bar[st]);
@@ -194,26 +283,25 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
         for (int t = 0; t < 4; ++t) bulk_g2s(stage[st] + (1 + t) * Mp, (const T *)a.in + t * plane + o, vbytes, &bar[st]);
     };
 
-    int cur = next_slot(blockIdx.x * kWarps + warp, nslots, nw, W, a.parity);
-    int r = 0, c = 0;
-    slot_node(cur, nslots, W, a.parity, r, c);
+    NodeWalk cur;
+    cur.init(blockIdx.x, gridDim.x, W, H, a.parity);
     uint32_t ph = 0, pending = 0;
     int st = 0;
-    if (cur < nslots) {
-        if (lane == 0) issue(r, c, 0);
+    if (cur.live()) {
+        if (lane == 0) issue(cur.r, cur.col(), 0);
         pending = 1;
     }
     bool ok = true;
-    while (cur < nslots) {
-        const int nxt = next_slot(cur + nw, nslots, nw, W, a.parity);
-        int rn = 0, cn = 0;
-        slot_node(nxt, nslots, W, a.parity, rn, cn);
-        if (nxt < nslots) {
+    while (cur.live()) {
+        const int r = cur.r, c = cur.col();
+        NodeWalk nxt = cur;
+        nxt.next();
+        if (nxt.live()) {
             // stage st ^ 1 was read by the previous node's phase 1; those reads
             // have returned (their values were consumed) and the warp has
             // synchronised since, so the copies may overwrite it
             __syncwarp();
-            if (lane == 0) issue(rn, cn, st ^ 1);
+            if (lane == 0) issue(nxt.r, nxt.col(), st ^ 1);
             pending |= 1u << (st ^ 1);
         }
         ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[st], (ph >> st) & 1u));
@@ -222,60 +310,25 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
         pending &= ~(1u << st);
 
         const bool has[4] = {c > 0, c < W - 1, r > 0, r < H - 1};
-        const T *sg = stage[st];
-
-        // phase 1: h of the four directions per label (Eq. 5), outer terms
         T S[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) S[t] = MIN ? (T)kBigE : (T)0;
-        for (int x0 = 4 * lane; x0 < Mp; x0 += 128) {
-            const V gv = *(const V *)(sg + x0);
-            V m[4];
+        if (M == Mp && has[0] && has[1] && has[2] && has[3])
+            form_h<MIN, true>(stage[st], h4, M, Mp, lane, has, S);
+        else
+            form_h<MIN, false>(stage[st], h4, M, Mp, lane, has, S);
+        if constexpr (MIN) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if constexpr (MIN)
-                    m[t] = has[t] ? *(const V *)(sg + (1 + t) * Mp + x0) : make_int4(0, 0, 0, 0);
-                else
-                    m[t] = has[t] ? *(const V *)(sg + (1 + t) * Mp + x0) : make_float4(1.f, 1.f, 1.f, 1.f);
-            }
-            const int sbase = (x0 & ~31) | (lane & 7);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const T m0 = comp(m[0], j), m1 = comp(m[1], j), m2 = comp(m[2], j), m3 = comp(m[3], j);
-                V hv;
-                if constexpr (MIN) {
-                    // padded labels (never a pattern column) stay out of the minima
-                    const int32_t tot = x0 + j < M ? comp(gv, j) + m0 + m1 + m2 + m3 : kBigE;
-                    hv = make_int4(tot - m0, tot - m1, tot - m2, tot - m3);
-                    S[0] = min(S[0], hv.x);
-                    S[1] = min(S[1], hv.y);
-                    S[2] = min(S[2], hv.z);
-                    S[3] = min(S[3], hv.w);
-                } else {
-                    const float g = x0 + j < M ? comp(gv, j) : 0.f;
-                    const float g01 = g * m0 * m1, g23 = g * m2 * m3;
-                    hv = make_float4(g23 * m1, g23 * m0, g01 * m3, g01 * m2);
-                    S[0] += hv.x;
-                    S[1] += hv.y;
-                    S[2] += hv.z;
-                    S[3] += hv.w;
-                }
-                h4[sbase + (j << 3)] = hv;
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if constexpr (MIN) {
-                S[t] = __reduce_min_sync(0xffffffffu, S[t]);
-            } else {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) S[t] += __shfl_xor_sync(0xffffffffu, S[t], o);
-            }
+            for (int t = 0; t < 4; ++t) S[t] = __reduce_min_sync(0xffffffffu, S[t]);
+        } else {
+            warp_sum4(S, lane);
         }
         __syncwarp();
 
         // phase 2: the band of every receiver label this lane owns, from the
-        // register pattern; step c outside, so KM independent chains
+        // register pattern; step c outside, so KM independent chains.  A hole
+        // reads a slot another lane reads with a value that changes nothing
+        // (0 in a sum, 2^29 in a minimum): no branch.
         V u[KM];
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
@@ -290,23 +343,18 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
                 const int i = k * LM + c2;
-                // a hole reads slot 0 with a value that changes nothing (0 in
-                // a sum, 2^29 in a minimum): no branch, so the gathers can be
-                // issued ahead of their use
                 const uint32_t off = (so[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
-                {
-                    const V hv = *(const V *)(hb + off);
-                    if constexpr (MIN) {
-                        u[k].x = __viaddmin_s32(wv[i], hv.x, u[k].x);
-                        u[k].y = __viaddmin_s32(wv[i], hv.y, u[k].y);
-                        u[k].z = __viaddmin_s32(wv[i], hv.z, u[k].z);
-                        u[k].w = __viaddmin_s32(wv[i], hv.w, u[k].w);
-                    } else {
-                        u[k].x = fmaf(wv[i], hv.x, u[k].x);
-                        u[k].y = fmaf(wv[i], hv.y, u[k].y);
-                        u[k].z = fmaf(wv[i], hv.z, u[k].z);
-                        u[k].w = fmaf(wv[i], hv.w, u[k].w);
-                    }
+                const V hv = *(const V *)(hb + off);
+                if constexpr (MIN) {
+                    u[k].x = __viaddmin_s32(wv[i], hv.x, u[k].x);
+                    u[k].y = __viaddmin_s32(wv[i], hv.y, u[k].y);
+                    u[k].z = __viaddmin_s32(wv[i], hv.z, u[k].z);
+                    u[k].w = __viaddmin_s32(wv[i], hv.w, u[k].w);
+                } else {
+                    u[k].x = fmaf(wv[i], hv.x, u[k].x);
+                    u[k].y = fmaf(wv[i], hv.y, u[k].y);
+                    u[k].z = fmaf(wv[i], hv.z, u[k].z);
+                    u[k].w = fmaf(wv[i], hv.w, u[k].w);
                 }
             }
         }
@@ -314,62 +362,63 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
         // combine, normalise (sum: divide by the total; min-sum: subtract the
         // minimum), store into the neighbours' planes
         T Z[4];
+        if constexpr (MIN) {
 #pragma unroll
-        for (int t = 0; t < 4; ++t) Z[t] = MIN ? (T)kBigE : (T)0;
+            for (int t = 0; t < 4; ++t) Z[t] = kBigE;
 #pragma unroll
-        for (int k = 0; k < KM; ++k) {
-            const int lk = (labp[k >> 1] >> ((k & 1) * 16)) & 0xFFFF;
-            if (lk < M) {
-                if constexpr (MIN) {
+            for (int k = 0; k < KM; ++k)
+                if (real & (1u << k)) {
                     Z[0] = min(Z[0], u[k].x);
                     Z[1] = min(Z[1], u[k].y);
                     Z[2] = min(Z[2], u[k].z);
                     Z[3] = min(Z[3], u[k].w);
-                } else {
+                }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) Z[t] = __reduce_min_sync(0xffffffffu, Z[t]);
+        } else {
+            // a padded label has no entries: its u stays 0 and adds nothing
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+                if (real & (1u << k)) {
                     u[k].x = fmaf(a.fbar, S[0], u[k].x);
                     u[k].y = fmaf(a.fbar, S[1], u[k].y);
                     u[k].z = fmaf(a.fbar, S[2], u[k].z);
                     u[k].w = fmaf(a.fbar, S[3], u[k].w);
-                    Z[0] += u[k].x;
-                    Z[1] += u[k].y;
-                    Z[2] += u[k].z;
-                    Z[3] += u[k].w;
                 }
-            }
-        }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if constexpr (MIN) {
-                Z[t] = __reduce_min_sync(0xffffffffu, Z[t]);
-            } else {
+            for (int t = 0; t < 4; ++t) Z[t] = 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) Z[t] += __shfl_xor_sync(0xffffffffu, Z[t], o);
+            for (int k = 0; k < KM; ++k) {
+                Z[0] += u[k].x;
+                Z[1] += u[k].y;
+                Z[2] += u[k].z;
+                Z[3] += u[k].w;
             }
+            warp_sum4(Z, lane);
         }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (!has[t]) continue;
             T *dst = (T *)a.out + dst_offset(t, r, c, W, plane, Mp);
-            if constexpr (MIN) {
+            T scale;
+            if constexpr (MIN)
+                scale = Z[t];
+            else
+                scale = __frcp_rn(Z[t]);   // the correctly rounded 1 / Z
 #pragma unroll
-                for (int k = 0; k < KM; ++k) {
-                    const int lk = (labp[k >> 1] >> ((k & 1) * 16)) & 0xFFFF;
-                    if (lk != 0xFFFF) dst[lk] = lk < M ? comp(u[k], t) - Z[t] : 0;
-                }
-            } else {
-                const float inv = __frcp_rn(Z[t]);   // the correctly rounded 1 / Z
-#pragma unroll
-                for (int k = 0; k < KM; ++k) {
-                    const int lk = (labp[k >> 1] >> ((k & 1) * 16)) & 0xFFFF;
-                    if (lk != 0xFFFF) dst[lk] = lk < M ? comp(u[k], t) * inv : 0.f;
+            for (int k = 0; k < KM; ++k) {
+                const int lk = (labp[k >> 1] >> ((k & 1) * 16)) & 0xFFFF;
+                if (all_lanes_labelled || lk != 0xFFFF) {
+                    if constexpr (MIN)
+                        dst[lk] = (real & (1u << k)) ? comp(u[k], t) - scale : 0;
+                    else
+                        dst[lk] = comp(u[k], t) * scale;   // padded labels: 0
                 }
             }
         }
         __syncwarp();   // the h slice is rewritten by the warp's next node
         st ^= 1;
         cur = nxt;
-        r = rn;
-        c = cn;
     }
     if (!ok) {
         if (lane == 0) atomicExch(a.status, 301);
@@ -383,7 +432,7 @@ __global__ void __launch_bounds__(kBlock, 2) sparse_reg_kernel(const SparseRegAr
 template <int KM, int LM, bool MIN>
 cudaError_t launch_reg(const SparseRegArgs &a, cudaStream_t s) {
     auto kern = sparse_reg_kernel<KM, LM, MIN>;
-    const size_t smem = (size_t)kWarps * warp_smem_bytes(a.d.Mp);
+    const size_t smem = warp_smem_bytes(a.d.Mp);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -391,8 +440,7 @@ cudaError_t launch_reg(const SparseRegArgs &a, cudaStream_t s) {
         per_sm = 1;
     const long long slots = a.parity < 0 ? (long long)a.d.W * a.d.H : (long long)((a.d.W + 1) / 2) * a.d.H;
     long long b = (long long)device_sm_count() * per_sm;
-    const long long need = (slots + kWarps - 1) / kWarps;
-    if (b > need) b = need;
+    if (b > slots) b = slots;
     kern<<<(int)(b < 1 ? 1 : b), kBlock, smem, s>>>(a);
     return cudaGetLastError();
 }

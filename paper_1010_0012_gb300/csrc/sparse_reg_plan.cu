@@ -47,13 +47,23 @@ struct QuarterCost {
     long long sq;   // sum of squared group counts (a tie-break toward even spreads)
 };
 
+// Lanes of a quarter-warp that read the same sender label at the same step
+// share one slot, so the bound counts distinct sender labels per bank group.
 QuarterCost quarter_cost(const std::vector<int> &pos, int q, int n, const std::vector<int> &len,
-                         const std::vector<int> &hist) {
+                         const std::vector<std::vector<int>> &senders) {
     int h[8] = {}, lmax = 0;
+    uint64_t seen[8] = {};   // sender labels < 512
     for (int i = 8 * q; i < std::min(n, 8 * q + 8); ++i) {
         const int x = pos[i];
         lmax = std::max(lmax, len[x]);
-        for (int g = 0; g < 8; ++g) h[g] += hist[x * 8 + g];
+        for (int xi : senders[x]) {
+            uint64_t &w = seen[xi >> 6];
+            const uint64_t b = 1ull << (xi & 63);
+            if (!(w & b)) {
+                w |= b;
+                ++h[reg_group(xi)];
+            }
+        }
     }
     QuarterCost c{lmax, 0};
     for (int g = 0; g < 8; ++g) {
@@ -74,8 +84,8 @@ long long partition_weight(const QuarterCost *qc, int nq) {
 
 // Split the n labels pos[] of one block into quarter-warps (positions 8q ..
 // 8q + 7) with evenly spread bank groups.
-void partition_block(std::vector<int> &pos, const std::vector<int> &len, const std::vector<int> &hist,
-                     XorShift &rng) {
+void partition_block(std::vector<int> &pos, const std::vector<int> &len,
+                     const std::vector<std::vector<int>> &senders, XorShift &rng) {
     const int n = (int)pos.size(), nq = (n + 7) / 8;
     std::stable_sort(pos.begin(), pos.end(), [&](int x, int y) { return len[x] > len[y]; });
     std::vector<int> dealt(n);
@@ -88,11 +98,11 @@ void partition_block(std::vector<int> &pos, const std::vector<int> &len, const s
     pos = dealt;
     if (nq < 2) return;
     QuarterCost qc[4];
-    for (int j = 0; j < nq; ++j) qc[j] = quarter_cost(pos, j, n, len, hist);
+    for (int j = 0; j < nq; ++j) qc[j] = quarter_cost(pos, j, n, len, senders);
     long long cur = partition_weight(qc, nq), best = cur;
     std::vector<int> best_pos = pos;
     double temp = 2.0 * (1 << 20);
-    for (int it = 0; it < 6000; ++it) {
+    for (int it = 0; it < 12000; ++it) {
         const int qa = (int)(rng.next() % nq);
         int qb = (int)(rng.next() % (nq - 1));
         if (qb >= qa) ++qb;
@@ -100,8 +110,8 @@ void partition_block(std::vector<int> &pos, const std::vector<int> &len, const s
         const int ib = 8 * qb + (int)(rng.next() % std::min(8, n - 8 * qb));
         std::swap(pos[ia], pos[ib]);
         const QuarterCost ca = qc[qa], cb = qc[qb];
-        qc[qa] = quarter_cost(pos, qa, n, len, hist);
-        qc[qb] = quarter_cost(pos, qb, n, len, hist);
+        qc[qa] = quarter_cost(pos, qa, n, len, senders);
+        qc[qb] = quarter_cost(pos, qb, n, len, senders);
         const long long w = partition_weight(qc, nq);
         if (w <= cur || rng.unit() < std::exp((double)(cur - w) / temp)) {
             cur = w;
@@ -154,8 +164,8 @@ int place_quarter(std::vector<int> &sched, const std::vector<std::vector<int>> &
     int best = cur;
     std::vector<int> best_sched = sched;
     double temp = 1.0;
-    const int iters = 2500 * nl;
-    for (int it = 0; it < iters && best > LM; ++it) {
+    const int iters = 10000 * nl;
+    for (int it = 0; it < iters && best > LM; ++it) {   // LM: one wavefront per step, the floor
         const int l = (int)(rng.next() % nl);
         const int a = (int)(rng.next() % LM);
         int b = (int)(rng.next() % (LM - 1));
@@ -175,7 +185,7 @@ int place_quarter(std::vector<int> &sched, const std::vector<std::vector<int>> &
         } else {
             std::swap(sched[l * LM + a], sched[l * LM + b]);
         }
-        temp = std::max(0.02, temp * 0.9997);
+        temp = std::max(0.02, temp * 0.99993);
     }
     sched = best_sched;
     return best;
@@ -187,12 +197,13 @@ bool sparse_reg_plan(int M, int Mp, const int32_t *rowptr, const int32_t *cols, 
                      SparseRegPlan *out) {
     if (Mp > 256 || Mp < 4) return false;
     const int KM = Mp <= 32 ? 1 : Mp / 32;
-    std::vector<int> len(Mp, 0), hist((size_t)Mp * 8, 0);
+    std::vector<int> len(Mp, 0);
+    std::vector<std::vector<int>> senders(Mp);
     int lmax = 0;
     for (int x = 0; x < M; ++x) {
         len[x] = rowptr[x + 1] - rowptr[x];
         lmax = std::max(lmax, len[x]);
-        for (int p = rowptr[x]; p < rowptr[x + 1]; ++p) ++hist[(size_t)x * 8 + reg_group(cols[p])];
+        senders[x].assign(cols + rowptr[x], cols + rowptr[x + 1]);
     }
     int LM = 0;
     for (const auto &v : kSparseRegVariants)
@@ -210,7 +221,7 @@ bool sparse_reg_plan(int M, int Mp, const int32_t *rowptr, const int32_t *cols, 
         const int base = 32 * k, n = std::min(32, Mp - base);
         std::vector<int> pos(n);
         for (int i = 0; i < n; ++i) pos[i] = base + i;
-        partition_block(pos, len, hist, rng);
+        partition_block(pos, len, senders, rng);
         for (int i = 0; i < n; ++i) out->lab[(size_t)k * 32 + i] = pos[i];
         for (int q = 0; q < 4; ++q) {
             std::vector<std::vector<int>> lists, where;   // sender labels / CSR positions per lane
