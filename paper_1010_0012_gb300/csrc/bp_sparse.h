@@ -14,9 +14,11 @@ namespace bpg {
 // memory slot of its sender label x_i, and the value bits) sits at
 // ell[i * M + x_j], i < len[x_j].
 //
-// Slot of label x in the kernels' per-warp h arrays: a rotation by x / 4
-// inside each group of four labels.
-inline int sp_label_slot(int x) { return (x & ~3) | ((x + (x >> 2)) & 3); }
+// Slot of label x in the list kernels' per-warp h arrays: a rotation by
+// x / 4 + x / 16 inside each group of four labels.  Lane l of a quarter-warp
+// stores label 4l + j to bank group 4 (l & 1) + ((j + l + l / 4) & 3): eight
+// different groups for the eight lanes.
+inline int sp_label_slot(int x) { return (x & ~3) | ((x + (x >> 2) + (x >> 4)) & 3); }
 struct SparseArgsF {
     const float *g;
     const float *in;

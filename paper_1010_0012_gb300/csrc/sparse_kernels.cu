@@ -23,7 +23,8 @@
 //
 // Shared-memory banks.  Label x lives in slot sp_label_slot(x) (bp_sparse.h),
 // a rotation inside each group of four labels that makes the phase-1 stores
-// of a quarter-warp hit eight different 16-byte bank groups.  The pattern
+// of a quarter-warp hit eight different 16-byte bank groups.  Where the
+// pattern fits, the register-pattern kernels (sparse_reg.cuh) run instead.  The pattern
 // holds slots, not labels, and the host orders each receiver label's entries
 // so that the eight lanes of a quarter-warp gather from different bank groups
 // at each step as far as a matching allows (the order of the terms of a sum
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kSpBlock) sparse_sum_kernel(const SparseArgsF 
                 const float m0 = comp(m[0], j), m1 = comp(m[1], j), m2 = comp(m[2], j), m3 = comp(m[3], j);
                 const float g01 = g * m0 * m1, g23 = g * m2 * m3;
                 const float4 hv = make_float4(g23 * m1, g23 * m0, g01 * m3, g01 * m2);
-                h4[x0 + ((j + lane) & 3)] = hv;   // slot of label x0 + j (sp_label_slot)
+                h4[x0 + ((j + lane + (lane >> 2)) & 3)] = hv;   // slot of label x0 + j (sp_label_slot)
                 S[0] += hv.x; S[1] += hv.y; S[2] += hv.z; S[3] += hv.w;
             }
         }
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kSpBlock) sparse_min_kernel(const SparseArgsI 
                 // padded labels (never a pattern column) stay out of the minima
                 const int32_t tot = x0 + j < M ? comp(ev, j) + m0 + m1 + m2 + m3 : kBigE;
                 const int4 hv = make_int4(tot - m0, tot - m1, tot - m2, tot - m3);
-                h4[x0 + ((j + lane) & 3)] = hv;   // slot of label x0 + j (sp_label_slot)
+                h4[x0 + ((j + lane + (lane >> 2)) & 3)] = hv;   // slot of label x0 + j (sp_label_slot)
                 hmin[0] = min(hmin[0], hv.x);
                 hmin[1] = min(hmin[1], hv.y);
                 hmin[2] = min(hmin[2], hv.z);
