@@ -671,20 +671,22 @@ def run_grid_workload(args, name):
 
 def gradient_floor_bytes(cfg, every=5):
     """HBM bytes the checkpointed gradient's launches must move: the recorded
-    forward (K log-domain iterations at 9 bytes per update), the checkpoint
-    copies (read and write one message state each), the recomputed states of
-    every segment (K minus one per segment) and K adjoint launches at 15 bytes
-    per node-label-direction (read l, log g, the adjoint in and d log g; write
-    the adjoint out and d log g).  Beliefs and their reverse are left out (one
-    launch each, under 2 %)."""
+    forward (K log-domain iterations at 9 bytes per update, its checkpoints
+    written in place), one copy of the starting state into the first
+    checkpoint, the recomputed states of every segment but the last (whose
+    states the forward keeps), and K adjoint launches at 15 bytes per
+    node-label-direction (read l, log g, the adjoint in and d log g; write the
+    adjoint out and d log g).  Beliefs, their reverse and the 8-byte scale per
+    message are left out (under 2 %)."""
     nodes = cfg.W * cfg.H
     De = wl.directed_edges(cfg.W, cfg.H)
     K = cfg.iters
     n_ck = (K + every - 1) // every
+    last_len = K - (n_ck - 1) * every
     fwd = (nodes * cfg.M + 2 * De * cfg.M) * 4
     adj = nodes * cfg.M * 15 * 4
     state = 4 * nodes * cfg.M * 4
-    parts = {"forward": K * fwd, "checkpoints": n_ck * 2 * state, "recompute": (K - n_ck) * fwd,
+    parts = {"forward": K * fwd, "checkpoints": 2 * state, "recompute": (K - n_ck - (last_len - 1)) * fwd,
              "adjoint": K * adj}
     return sum(parts.values()), parts
 

@@ -11,12 +11,18 @@
 //   da(x_i)   = dh(x_i) h(x_i)   -> dL/d log g_i and dL/d l_ki for every k != j
 //   dw(d)    += sum_{x_j} nu(x_j) h(x_j + d)                           (= dL/df(d))
 //   dfbar    += S sum_x nu(x) - sum_d dw(d)   (fbar enters u directly and through w)
-// The common factor exp(A) of h, u, Z and nu cancels in every product above.
-// The states and log g are base-2 logs (the library's log domain): h and the
+// In terms of the normalised h^ = h / Z, S^ = S / Z, u^ = u / Z and
+// nu^ = Z nu = delta / u^ - sum delta, every line keeps its form:
+//   da = h^ (sum_e w(-e) nu^(x + e) + fbar sum nu^),  dw(d) += sum nu^ h^(x_j + d),
+//   dfbar += S^ sum nu^ - sum_d dw(d).
+// The recorded forward stores per message C = A + log2 Z and S^ (the stats
+// planes), so h^ = 2^(a - C) comes without the max, S and Z reductions of
+// the forward; only sum delta and sum nu^ are reduced here.
+// The states and log g are base-2 logs (the library's log domain): h^ and the
 // belief softmax are computed with 2^x exactly as the forward kernel does,
 // while every adjoint (delta, nu, da, dL/d log g) is a derivative with
 // respect to natural logs, the units of the caller's log g and log-beliefs.
-// delta / u uses the hardware approximate division (2 ulp; u > 0 is normal).
+// delta / u^ uses the hardware approximate division (2 ulp; u^ > 0 is normal).
 //
 // One kernel launch reverses one synchronous iteration for every node; the
 // per-block sums of dw and dfbar go to a scratch row per (iteration, block),
@@ -30,6 +36,9 @@
 #include "bp_adjoint.h"
 
 namespace bpg {
+
+// scale of an absent message: 2^(a - kNoScale) = 0
+constexpr float kNoScale = 3.0e38f;
 
 // One chunk per lane and T <= 4 (kEarly): the kernel is held to 80 registers
 // so that three blocks (24 warps) share an SM, and every load of a node is
@@ -55,18 +64,9 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
 #pragma unroll
     for (int i = 0; i < 2 * T + 1; ++i) w[i] = a.w[i];
     const float fbar = a.fbar;
-    float cz[V];
     bool lab_ok[V];
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        const int x = q * V + k;
-        float cx = 0.f;
-#pragma unroll
-        for (int d = -T; d <= T; ++d)
-            if (x - d >= 0 && x - d < M) cx += w[d + T];
-        lab_ok[k] = x < M;
-        cz[k] = lab_ok[k] ? cx + (float)M * fbar : 0.f;
-    }
+    for (int k = 0; k < V; ++k) lab_ok[k] = q * V + k < M;
 
     float pacc[NP];
 #pragma unroll
@@ -98,6 +98,15 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
             }
             if (valid) ld_vec<V>(dgo, a.dlogg + off); else fill_vec<V>(dgo, 0.f);
         }
+        // the forward's scale and S^ of each outgoing message (absent: h^ = 0)
+        const long long node = (long long)r * W + c, nodes = (long long)W * H;
+        float Cs[4], Sh[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float2 sv = has[t] ? __ldg(a.stats + t * nodes + node) : make_float2(0.f, 0.f);
+            Cs[t] = has[t] ? sv.x : kNoScale;
+            Sh[t] = sv.y;
+        }
         float dl[4][V], dg[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -108,28 +117,16 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
 
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            // forward recompute of the message towards neighbour t
+            // h^ of the message towards neighbour t, from the stored scale
             float h[V];
-            float amax = kLogNone;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 float s = gam[k];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (u != t) s += l[u][k];
-                h[k] = (FULL || lab_ok[k]) ? s : kLogNone;
-                amax = fmaxf(amax, h[k]);
+                h[k] = (FULL || lab_ok[k]) ? exp2_hw(s - Cs[t]) : 0.f;   // as the forward kernel
             }
-            amax = group_max<L>(amax);
-            float S = 0.f, Z = 0.f;
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                h[k] = (FULL || lab_ok[k]) ? exp2_hw(h[k] - amax) : 0.f;   // as the forward kernel
-                S += h[k];
-                Z = fmaf(h[k], cz[k], Z);
-            }
-            S = group_sum<L>(S);
-            Z = group_sum<L>(Z);
             float win[V + 2 * T];
             band_window<L, V, T, float>(win, h, q, 0.f);
 
@@ -149,15 +146,14 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
                 nd += del[k];
             }
             nd = group_sum<L>(nd);
-            const float invZ = 1.f / Z;
             float nu[V];
             float nn = 0.f;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                float u = fbar * S;
+                float u = fbar * Sh[t];
 #pragma unroll
                 for (int d = -T; d <= T; ++d) u = fmaf(w[d + T], win[T + k + d], u);
-                nu[k] = (FULL || lab_ok[k]) ? __fdividef(del[k], u) - nd * invZ : 0.f;
+                nu[k] = ((FULL || lab_ok[k]) && has[t]) ? __fdividef(del[k], u) - nd : 0.f;
                 nn += nu[k];
             }
             nn = group_sum<L>(nn);
@@ -170,7 +166,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
                 float dh = fbar * nn;
 #pragma unroll
                 for (int e = -T; e <= T; ++e) dh = fmaf(w[-e + T], nwin[T + k + e], dh);
-                const float da = (FULL || lab_ok[k]) ? dh * h[k] : 0.f;
+                const float da = dh * h[k];
                 dg[k] += da;
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
@@ -187,7 +183,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
                 pacc[d + T] += acc;
                 dsum += acc;
             }
-            pacc[NP - 1] += (q == 0 ? nn * S : 0.f) - dsum;
+            pacc[NP - 1] += (q == 0 ? nn * Sh[t] : 0.f) - dsum;
         }
 
 #pragma unroll

@@ -237,7 +237,8 @@ struct SumBand {
     }
 
     __device__ __forceinline__ void node(const float *g, const float *in, float *out, int W, int H, int Mp,
-                                         long long plane, int r, int c, bool valid) const {
+                                         long long plane, int r, int c, bool valid,
+                                         float2 *stats = nullptr) const {
         const long long off = ((long long)r * W + c) * Mp + q * V;
         const bool has[4] = {valid && c > 0, valid && c < W - 1, valid && r > 0, valid && r < H - 1};
         const float absent = LOG ? 0.f : 1.f;
@@ -253,6 +254,7 @@ struct SumBand {
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             float h[V];
+            float amax = 0.f;   // log mode: the max shift of h
             if (!LOG) {
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
@@ -262,7 +264,7 @@ struct SumBand {
                     h[k] = gv[k] * p01 * p23;
                 }
             } else {
-                float amax = kLogNone;
+                amax = kLogNone;
 #pragma unroll
                 for (int k = 0; k < V; ++k) {
                     float s = gv[k];
@@ -290,6 +292,11 @@ struct SumBand {
             band_window<L, V, T, float>(win, h, q, 0.f);
             const float inv = 1.f / Z;
             const float base_term = fbar * S * inv;
+            if constexpr (LOG) {
+                // the scale of this message for the adjoint: h / Z = 2^(a - C)
+                if (stats && q == 0 && has[t])
+                    stats[(long long)t * W * H + (long long)r * W + c] = make_float2(amax + __log2f(Z), S * inv);
+            }
             float o[V];
 #pragma unroll
             for (int k = 0; k < V; ++k) {
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
     for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
         int r, c;
         const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
-        band.node(a.g, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid);
+        band.node(a.g, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid, LOG ? a.stats : nullptr);
     }
 }
 

@@ -1,10 +1,11 @@
 // Recorded log-domain forward (checkpoints) and its reverse (bp_backward).
 //
 // Forward with BP_RECORD: the message state entering iterations 0, c, 2c, ...
-// is copied to a checkpoint (c = checkpoint interval).  Backward walks the
-// segments from the last to the first: it recomputes the states of a segment
-// from its checkpoint with the same forward kernel (so bit-identical to the
-// recorded run), then applies the adjoint kernel once per iteration in
+// is kept as a checkpoint (c = checkpoint interval), and the last segment's
+// states are kept whole.  Backward walks the segments from the last to the
+// first: it recomputes the states of a segment from its checkpoint with the
+// same forward kernel (so bit-identical to the recorded run; the last segment
+// needs none), then applies the adjoint kernel once per iteration in
 // reverse, accumulating dL/d log g and per-block sums of dL/df(d), dL/dfbar;
 // those sums are reduced over all blocks and iterations in FP64.
 #include <cuda_runtime.h>
@@ -23,7 +24,7 @@ void bpg_free_extras(bp_ctx *h) {
         if (p) cudaFree(p);
     h->ckpts.clear();
     void *bufs[] = {h->seg_buf, h->adj[0], h->adj[1], h->dtab_partial, h->tc_a, h->tc_b, h->tc_z, h->dlogg_pad,
-                    h->d_red, h->p_mrf, h->p_items[0], h->p_items[1], h->p_bar, h->ms_logu};
+                    h->d_red, h->p_mrf, h->p_items[0], h->p_items[1], h->p_bar, h->ms_logu, h->stats_buf};
     for (void *p : bufs)
         if (p) cudaFree(p);
 }
@@ -47,6 +48,25 @@ static BandArgsF log_args(bp_ctx *h, const void *in, void *out) {
     return a;
 }
 
+// The states of a segment after its checkpoint (c - 1 of them) live in one buffer.
+static bp_status ensure_segment_buffer(bp_ctx *h, int c) {
+    const int seg_states = c > 1 ? c - 1 : 1;
+    if (h->seg_cap >= seg_states) return BP_OK;
+    if (h->seg_buf) {
+        cudaFree(h->seg_buf);
+        h->seg_buf = nullptr;
+    }
+    h->seg_cap = 0;
+    if (bp_status st = bpg_ensure_buffer(h, &h->seg_buf, bpg_state_bytes(h) * seg_states, "segment states")) return st;
+    h->seg_cap = seg_states;
+    return BP_OK;
+}
+
+// The recorded forward writes each checkpoint directly: the iteration that
+// ends at t = c, 2c, ... stores its output in that checkpoint, and the next
+// iteration reads it from there.  Only the state entering iteration 0 is
+// copied.  The states of the last segment after its checkpoint go to the
+// segment buffer, where the backward finds them without recomputing.
 bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
     const int c = h->ckpt_every;
     const int n_ck = (n_iters + c - 1) / c;
@@ -56,17 +76,41 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
         if (bp_status st = bpg_ensure_buffer(h, &p, sb, "checkpoint")) return st;
         h->ckpts.push_back(p);
     }
-    for (int t = 0; t < n_iters; ++t) {
-        if (t % c == 0)
-            BK_CK(h, cudaMemcpyAsync(h->ckpts[t / c], h->msg[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream));
-        BK_CK(h, launch_band_log(log_args(h, h->msg[h->cur], h->msg[h->cur ^ 1]), h->log_layout, h->blocks_override,
-                                 h->stream));
-        h->cur ^= 1;
-        h->launches += 1;
+    if (bp_status st = ensure_segment_buffer(h, c)) return st;
+    const size_t stats_per_iter = (size_t)4 * h->W * h->H;   // float2 per message
+    const size_t stats_bytes = stats_per_iter * sizeof(float2) * (n_iters > 0 ? n_iters : 1);
+    if (h->stats_cap < stats_bytes) {
+        if (h->stats_buf) {
+            cudaFree(h->stats_buf);
+            h->stats_buf = nullptr;
+        }
+        h->stats_cap = 0;
+        if (bp_status st = bpg_ensure_buffer(h, &h->stats_buf, stats_bytes, "forward scales")) return st;
+        h->stats_cap = stats_bytes;
     }
+    const int last_start = (n_ck - 1) * c;
+    void *state = h->msg[h->cur];
+    if (n_iters > 0) BK_CK(h, cudaMemcpyAsync(h->ckpts[0], state, sb, cudaMemcpyDeviceToDevice, h->stream));
+    for (int t = 0; t < n_iters; ++t) {
+        const int t1 = t + 1;   // the state this iteration produces enters iteration t1
+        void *out;
+        if (t1 < n_iters && t1 % c == 0)
+            out = h->ckpts[t1 / c];
+        else if (t1 < n_iters && t1 > last_start)
+            out = (char *)h->seg_buf + (size_t)(t1 - last_start - 1) * sb;
+        else
+            out = state == h->msg[0] ? h->msg[1] : h->msg[0];
+        BandArgsF la = log_args(h, state, out);
+        la.stats = (float2 *)h->stats_buf + (size_t)t * stats_per_iter;
+        BK_CK(h, launch_band_log(la, h->log_layout, h->blocks_override, h->stream));
+        h->launches += 1;
+        state = out;
+    }
+    h->cur = state == h->msg[0] ? 0 : 1;
     h->rec_iters = n_iters;
     h->rec_every = c;
     h->recorded = true;
+    h->last_seg_kept = n_iters > 0;
     return BP_OK;
 }
 
@@ -85,12 +129,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
     const long long nodes = (long long)h->W * h->H;
     const int blocks = adjoint_blocks(h->dims, h->log_layout, Teff);
     if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: no adjoint kernel for this layout");
-    const int seg_states = c > 1 ? c - 1 : 1;
-    if (h->seg_cap < seg_states) {
-        if (h->seg_buf) { cudaFree(h->seg_buf); h->seg_buf = nullptr; }
-        if (bp_status st = bpg_ensure_buffer(h, &h->seg_buf, sb * seg_states, "segment states")) return st;
-        h->seg_cap = seg_states;
-    }
+    if (bp_status st = ensure_segment_buffer(h, c)) return st;
     if (bp_status st = bpg_ensure_buffer(h, &h->adj[0], sb, "adjoint state")) return st;
     if (bp_status st = bpg_ensure_buffer(h, &h->adj[1], sb, "adjoint state")) return st;
     if (bp_status st = bpg_ensure_buffer(h, &h->dlogg_pad, (size_t)nodes * h->Mp * 4, "dlogg")) return st;
@@ -114,11 +153,16 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
     for (int seg = n_ck - 1; seg >= 0; --seg) {
         const int start = seg * c, end = std::min(K, start + c), len = end - start;
         states[0] = h->ckpts[seg];
+        // the last segment's states are still in the segment buffer from the
+        // recorded run (unless a previous backward has overwritten it)
+        const bool kept = seg == n_ck - 1 && h->last_seg_kept;
         for (int j = 1; j < len; ++j) {
             states[j] = (char *)h->seg_buf + (size_t)(j - 1) * sb;
+            if (kept) continue;
             BK_CK(h, launch_band_log(log_args(h, states[j - 1], states[j]), h->log_layout, h->blocks_override, h->stream));
             h->launches += 1;
         }
+        h->last_seg_kept = false;   // the next segment's recompute overwrites the buffer
         for (int t = end - 1; t >= start; --t) {
             AdjArgs a{};
             a.logg = h->log_unary;
@@ -127,6 +171,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
             a.lam = (float *)h->adj[ca ^ 1];
             a.dlogg = (float *)h->dlogg_pad;
             a.partial = (float *)h->dtab_partial + (size_t)t * blocks * NP;
+            a.stats = (const float2 *)h->stats_buf + (size_t)t * 4 * nodes;
             a.d = h->dims;
             a.T = Teff;
             for (int i = 0; i < 2 * Teff + 1; ++i) a.w[i] = h->wf[i];

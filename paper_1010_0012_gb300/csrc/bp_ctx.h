@@ -85,6 +85,9 @@ struct bp_ctx {
     std::vector<void *> ckpts;      // states at t = 0, every, 2 every, ...
     void *seg_buf = nullptr;        // recomputed states of one segment
     int seg_cap = 0;
+    bool last_seg_kept = false;     // seg_buf holds the recorded run's last segment
+    void *stats_buf = nullptr;      // [iterations][4][H][W] float2 (C, S/Z) of the recorded run
+    size_t stats_cap = 0;
     void *adj[2] = {nullptr, nullptr};   // adjoint message states
     void *dtab_partial = nullptr;   // per-(iteration, block) partial sums of d table, d fbar
     size_t dtab_cap = 0;

@@ -60,9 +60,10 @@ def test_algorithmic_bytes_and_units_of_the_benchmark_workload():
 
 
 def test_gradient_floor_counts_each_launch_of_the_checkpointed_schedule():
-    """256x256, M = 64, K = 30, checkpoint 5: 30 recorded and 24 recomputed
-    forward launches at (W H M + 2 De M) * 4 bytes, 30 adjoint launches at
-    15 words per node-label, 6 checkpoint copies of a 4-plane state."""
+    """256x256, M = 64, K = 30, checkpoint 5: 30 recorded forward launches
+    and 20 recomputed ones (segments 0..4 recompute 4 states each; the last
+    segment's states are kept) at (W H M + 2 De M) * 4 bytes, 30 adjoint
+    launches at 15 words per node-label, one copy of a 4-plane state."""
     import bench
     from paper_1010_0012_gb300 import workload as wl
     cfg = wl.CONFIGS["grid256_m64_grad"]
@@ -70,9 +71,9 @@ def test_gradient_floor_counts_each_launch_of_the_checkpointed_schedule():
     De = 2 * (256 * 255 + 256 * 255)
     fwd = (256 * 256 * 64 + 2 * De * 64) * 4
     assert fwd == 150_470_656
-    assert parts["forward"] == 30 * fwd and parts["recompute"] == 24 * fwd
+    assert parts["forward"] == 30 * fwd and parts["recompute"] == 20 * fwd
     assert parts["adjoint"] == 30 * 256 * 256 * 64 * 60
-    assert parts["checkpoints"] == 6 * 2 * 4 * 256 * 256 * 64 * 4
+    assert parts["checkpoints"] == 2 * 4 * 256 * 256 * 64 * 4
     assert total == sum(parts.values())
 
 
