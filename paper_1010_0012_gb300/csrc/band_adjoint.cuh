@@ -99,14 +99,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
             if (valid) ld_vec<V>(dgo, a.dlogg + off); else fill_vec<V>(dgo, 0.f);
         }
         // the forward's scale and S^ of each outgoing message (absent: h^ = 0)
-        const long long node = (long long)r * W + c, nodes = (long long)W * H;
-        float Cs[4], Sh[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const float2 sv = has[t] ? __ldg(a.stats + t * nodes + node) : make_float2(0.f, 0.f);
-            Cs[t] = has[t] ? sv.x : kNoScale;
-            Sh[t] = sv.y;
-        }
+        const float2 *sp = a.stats + ((long long)r * W + c) * 4;
         float dl[4][V], dg[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -118,6 +111,12 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             // h^ of the message towards neighbour t, from the stored scale
+            float Ct = kNoScale, St = 0.f;
+            if (has[t]) {
+                const float2 sv = __ldg(sp + t);
+                Ct = sv.x;
+                St = sv.y;
+            }
             float h[V];
 #pragma unroll
             for (int k = 0; k < V; ++k) {
@@ -125,7 +124,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (u != t) s += l[u][k];
-                h[k] = (FULL || lab_ok[k]) ? exp2_hw(s - Cs[t]) : 0.f;   // as the forward kernel
+                h[k] = (FULL || lab_ok[k]) ? exp2_hw(s - Ct) : 0.f;   // as the forward kernel
             }
             float win[V + 2 * T];
             band_window<L, V, T, float>(win, h, q, 0.f);
@@ -150,7 +149,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
             float nn = 0.f;
 #pragma unroll
             for (int k = 0; k < V; ++k) {
-                float u = fbar * Sh[t];
+                float u = fbar * St;
 #pragma unroll
                 for (int d = -T; d <= T; ++d) u = fmaf(w[d + T], win[T + k + d], u);
                 nu[k] = ((FULL || lab_ok[k]) && has[t]) ? __fdividef(del[k], u) - nd : 0.f;
@@ -183,7 +182,7 @@ __device__ __forceinline__ void adjoint_body(const AdjArgs &a) {
                 pacc[d + T] += acc;
                 dsum += acc;
             }
-            pacc[NP - 1] += (q == 0 ? nn * Sh[t] : 0.f) - dsum;
+            pacc[NP - 1] += (q == 0 ? nn * St : 0.f) - dsum;
         }
 
 #pragma unroll

@@ -14,7 +14,7 @@ struct AdjArgs {
     float *lam;             // [4][H][W][Mp] dL/d(messages entering iteration t)
     float *dlogg;           // [H][W][Mp] dL/d log g, accumulated
     float *partial;         // [blocks][2T + 2] per-block sums of dL/df(d) and dL/dfbar
-    const float2 *stats;    // [4][H][W] (C, S^) of each message of iteration t, from the recorded forward
+    const float2 *stats;    // [H][W][4] (C, S^) of each message of iteration t, from the recorded forward
     GridDims d;
     int T;
     float w[2 * kTMaxFast + 1];   // f(d) - fbar

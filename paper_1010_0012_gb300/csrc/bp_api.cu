@@ -354,12 +354,14 @@ bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_h
     if (h->layout.C == 2 && (long long)W * H * (Mp / 8) < 4LL * device_sm_count() * 2048)
         for (int i = 0; i < nlay; ++i)
             if (lays[i].C == 1) { h->layout = lays[i]; break; }
-    // the log-domain kernels (an exp per h entry, a log per output, and the
-    // adjoint's extra state per label) keep one chunk per lane: the same
-    // rounding path for the recorded forward and its adjoint
+    // the log-domain forward (recorded and recomputed alike) takes the same
+    // layout; the adjoint, which holds more state per label, one chunk per
+    // lane (it reads the states and the forward's scales, whatever layout
+    // made them)
     h->log_layout = h->layout;
+    h->adj_layout = h->layout;
     for (int i = 0; i < nlay; ++i)
-        if (lays[i].C == 1) h->log_layout = lays[i];
+        if (lays[i].C == 1) h->adj_layout = lays[i];
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { bp_status st = cuda_fail(nullptr, e, "cudaGetDevice"); delete h; return st; }
     if (cuda_stream) {

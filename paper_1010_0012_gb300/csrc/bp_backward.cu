@@ -77,7 +77,7 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
         h->ckpts.push_back(p);
     }
     if (bp_status st = ensure_segment_buffer(h, c)) return st;
-    const size_t stats_per_iter = (size_t)4 * h->W * h->H;   // float2 per message
+    const size_t stats_per_iter = (size_t)4 * h->W * h->H;   // float2 per message, [H][W][4]
     const size_t stats_bytes = stats_per_iter * sizeof(float2) * (n_iters > 0 ? n_iters : 1);
     if (h->stats_cap < stats_bytes) {
         if (h->stats_buf) {
@@ -89,6 +89,7 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
         h->stats_cap = stats_bytes;
     }
     const int last_start = (n_ck - 1) * c;
+    h->rec_layout = h->log_layout;
     void *state = h->msg[h->cur];
     if (n_iters > 0) BK_CK(h, cudaMemcpyAsync(h->ckpts[0], state, sb, cudaMemcpyDeviceToDevice, h->stream));
     for (int t = 0; t < n_iters; ++t) {
@@ -102,7 +103,7 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
             out = state == h->msg[0] ? h->msg[1] : h->msg[0];
         BandArgsF la = log_args(h, state, out);
         la.stats = (float2 *)h->stats_buf + (size_t)t * stats_per_iter;
-        BK_CK(h, launch_band_log(la, h->log_layout, h->blocks_override, h->stream));
+        BK_CK(h, launch_band_log(la, h->rec_layout, h->blocks_override, h->stream));
         h->launches += 1;
         state = out;
     }
@@ -127,7 +128,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
     const int K = h->rec_iters, c = h->rec_every, Teff = h->Teff, NP = 2 * Teff + 2;
     const size_t sb = bpg_state_bytes(h);
     const long long nodes = (long long)h->W * h->H;
-    const int blocks = adjoint_blocks(h->dims, h->log_layout, Teff);
+    const int blocks = adjoint_blocks(h->dims, h->adj_layout, Teff);
     if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: no adjoint kernel for this layout");
     if (bp_status st = ensure_segment_buffer(h, c)) return st;
     if (bp_status st = bpg_ensure_buffer(h, &h->adj[0], sb, "adjoint state")) return st;
@@ -159,7 +160,8 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
         for (int j = 1; j < len; ++j) {
             states[j] = (char *)h->seg_buf + (size_t)(j - 1) * sb;
             if (kept) continue;
-            BK_CK(h, launch_band_log(log_args(h, states[j - 1], states[j]), h->log_layout, h->blocks_override, h->stream));
+            BK_CK(h, launch_band_log(log_args(h, states[j - 1], states[j]), h->rec_layout, h->blocks_override,
+                                     h->stream));
             h->launches += 1;
         }
         h->last_seg_kept = false;   // the next segment's recompute overwrites the buffer
@@ -176,7 +178,7 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
             a.T = Teff;
             for (int i = 0; i < 2 * Teff + 1; ++i) a.w[i] = h->wf[i];
             a.fbar = h->fbarf;
-            BK_CK(h, launch_band_log_adjoint(a, h->log_layout, blocks, h->stream));
+            BK_CK(h, launch_band_log_adjoint(a, h->adj_layout, blocks, h->stream));
             h->launches += 1;
             ca ^= 1;
         }

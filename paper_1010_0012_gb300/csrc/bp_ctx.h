@@ -68,6 +68,8 @@ struct bp_ctx {
 
     bpg::Layout layout{32, 1};
     bpg::Layout log_layout{32, 1};  // layout of the log-domain forward and adjoint kernels
+    bpg::Layout adj_layout{32, 1};  // layout of the adjoint kernel (reads states and scales, any layout)
+    bpg::Layout rec_layout{32, 1};  // log layout of the recorded run (its recompute must match it bit for bit)
     bool fast = false;              // register/shuffle kernels serve (M, T)
     int blocks_override = 0;
     bool use_graphs = true;

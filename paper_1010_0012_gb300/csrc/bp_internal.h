@@ -31,7 +31,7 @@ struct BandArgsF {
     int T;
     float w[2 * kTMaxFast + 1];  // f(d) - fbar, d = -T..T
     float fbar;
-    // log mode only, nullable: per message [4][H][W] the forward's scale
+    // log mode only, nullable: per message [H][W][4] the forward's scale
     // C = A + log2 Z (A the max shift, Z the normaliser) and S / Z, read by
     // the adjoint kernel instead of recomputing them
     float2 *stats;
