@@ -251,7 +251,6 @@ struct SumBand {
             else fill_vec<V>(m[s], absent);
         }
 
-        float st_amax[4], st_z[4], st_s[4];   // log mode: each message's shift, normaliser, S / Z
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             float h[V];
@@ -294,9 +293,11 @@ struct SumBand {
             const float inv = 1.f / Z;
             const float base_term = fbar * S * inv;
             if constexpr (LOG) {
-                st_amax[t] = amax;
-                st_z[t] = Z;
-                st_s[t] = S * inv;
+                // the scale of this message for the adjoint, [node][direction]:
+                // h / Z = 2^(a - C), C = shift + log2 Z; lane t of the group
+                // writes direction t (a node's four pairs fill one 32-byte sector)
+                if (stats && valid && q == (t & (L - 1)))
+                    stats[((long long)r * W + c) * 4 + t] = make_float2(amax + __log2f(Z), S * inv);
             }
             float o[V];
 #pragma unroll
@@ -308,17 +309,6 @@ struct SumBand {
                 o[k] = (FULL || lab_ok[k]) ? (LOG ? __log2f(mv) : mv) : 0.f;
             }
             if (has[t]) st_vec<V>(out + out_offset(t, r, c, W, plane, Mp) + q * V, o);
-        }
-        if constexpr (LOG) {
-            // the scale of each message for the adjoint, [node][direction]:
-            // h / Z = 2^(a - C), C = shift + log2 Z; lane t of the group writes
-            // direction t, so a node's four pairs are one 32-byte store
-            if (stats && valid) {
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (q == (t & (L - 1)))
-                        stats[((long long)r * W + c) * 4 + t] = make_float2(st_amax[t] + __log2f(st_z[t]), st_s[t]);
-            }
         }
     }
 };
