@@ -55,17 +55,35 @@ def log_beliefs(logg, table, fbar, grid, T, n_iters, every=5):
     return BPFunction.apply(logg, table, fbar, grid, T, n_iters, every)
 
 
+class _NegScaledCost(torch.autograd.Function):
+    """log g = -beta * cost.  The forward multiplies in FP32: the product of
+    two FP32 numbers is exact in FP64, so rounding it once to FP32 gives what
+    an FP64 product rounded to FP32 gives.  The backward keeps the chain rule
+    to beta, a sum over every node and label, in FP64 (products and sum)."""
+
+    @staticmethod
+    def forward(ctx, cost, beta):
+        ctx.save_for_backward(cost, beta)
+        return torch.mul(cost, beta.to(device=cost.device, dtype=cost.dtype)).neg_()
+
+    @staticmethod
+    def backward(ctx, dlogg):
+        cost, beta = ctx.saved_tensors
+        g = -torch.dot(dlogg.reshape(-1).double(), cost.reshape(-1).double())
+        return None, g.to(device=beta.device, dtype=beta.dtype)
+
+
 def stereo_nll(cost, d_gt, alpha, fbar, beta, T, n_iters, grid, every=5):
     """-sum_i log b_i(x_i*) of the stereo model (Sec. 6) with parameters
     alpha, fbar, beta as tensors: log g = -beta cost, f(d) = exp(-alpha |d|)
     for |d| <= T and fbar outside.  Autograd's chain rule maps the library's
     dL/d log g, dL/df(d), dL/dfbar to dL/d beta, d alpha, d fbar."""
     dev = cost.device
-    # the chain rule to beta sums dL/d log g * cost over every node: keep that
-    # reduction in FP64 (the library's log g stays FP32)
-    logg = (-beta.to(dev).double() * cost.double()).float()
+    # the chain rule to beta sums dL/d log g * cost over every node: that
+    # reduction stays in FP64 (the library's log g is FP32)
+    logg = _NegScaledCost.apply(cost.float().contiguous(), beta)
     d = torch.arange(-T, T + 1, dtype=torch.float32, device=alpha.device).abs()
     table = torch.exp(-alpha * d)
-    logb = log_beliefs(logg.float().contiguous(), table, fbar, grid, T, n_iters, every)
+    logb = log_beliefs(logg, table, fbar, grid, T, n_iters, every)
     idx = torch.as_tensor(d_gt, dtype=torch.long, device=dev)[..., None]
     return -torch.gather(logb, -1, idx).sum()
