@@ -518,19 +518,20 @@ def run_batch_workload(args):
     print(json.dumps(line))
 
 
-def run_dense_compare_workload(args):
+def measure_dense_compare(args, pairs=((64, 3), (128, 4), (256, 4)), cuda_core=True, reps=5):
     """The O(mM) update against the O(M^2) baselines on the same 1280x720
-    grid at M = 64 (T = 3) and M = 128 (T = 4): time per synchronous
-    sum-product iteration of each (CUDA events, median of 5 runs of 5
-    iterations after a warm-up run)."""
+    grid at each (M, T): time per synchronous sum-product iteration of each
+    (CUDA events on the handle's stream, median of `reps` runs after a
+    warm-up run), with the sampled clocks of the region."""
     import dataclasses
     import torch
     from paper_1010_0012_gb300 import bp
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
     pk = peaks()
     out = {}
-    for M, T in ((64, 3), (128, 4)):
+    for M, T in pairs:
         cfg = dataclasses.replace(wl.CONFIGS["grid1280x720_m128"], M=M, T=T)
         st = wl.make_stereo(cfg)
         u = torch.from_numpy(wl.unary_f32(st)).cuda()
@@ -539,42 +540,62 @@ def run_dense_compare_workload(args):
         G.set_unary(u)
         tab, fbar = wl.pair_table_f32(cfg.alpha, T)
         G.set_potential(tab, T, fbar)
-        n_it = 5
-        runs = {"band_mM": lambda: G.iterate(n_it, bp.BP_SUM, "sync")}
-        for name, kind in (("dense_bf16_tcgen05_fused", bp.BP_DENSE_BF16_TC_FUSED),
-                           ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC),
-                           ("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE)):
-            runs[name] = (lambda k: (lambda: bp.bp_iterate_dense(G.h, n_it, k)))(kind)
+        kinds = [("band_mM", None, 5), ("dense_bf16_tcgen05_fused", bp.BP_DENSE_BF16_TC_FUSED, 5),
+                 ("dense_bf16_tcgen05", bp.BP_DENSE_BF16_TC, 5)]
+        if cuda_core:
+            kinds.append(("dense_fp32_cuda_core", bp.BP_DENSE_CUDA_CORE, 1 if M > 128 else 5))
         res = {}
-        for name, fn in runs.items():
-            G.reset()
-            G.iterate(0, bp.BP_SUM, "sync")
-            fn()
-            G.sync()
-            ts = []
-            for _ in range(5):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                b.synchronize()
-                ts.append(a.elapsed_time(b) / 1e3 / n_it)
-            t = statistics.median(ts)
-            ach = algorithmic_bytes(cfg) / t / 1e9
-            res[name] = {"value": workload_units(cfg) / t, "unit": UNIT, "ms_per_iter": t * 1e3,
-                         "hbm_frac_at_9_bytes_per_update": ach / pk["hbm_gbs"]}
-        G.sync()
-        res["band_over_fused_tcgen05"] = res["band_mM"]["value"] / res["dense_bf16_tcgen05_fused"]["value"]
+        with ClockSampler(dev) as clk:
+            clk.wait_ready()
+            for name, kind, n_it in kinds:
+                if kind is None:
+                    fn = (lambda n: (lambda: G.iterate(n, bp.BP_SUM, "sync")))(n_it)
+                else:
+                    fn = (lambda k, n: (lambda: bp.bp_iterate_dense(G.h, n, k)))(kind, n_it)
+                try:
+                    G.reset()
+                    G.iterate(0, bp.BP_SUM, "sync")
+                    fn()
+                    G.sync()
+                    ts = []
+                    for _ in range(reps):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        fn()
+                        b.record(stream)
+                        b.synchronize()
+                        ts.append(a.elapsed_time(b) / 1e3 / n_it)
+                    G.sync()
+                except bp.BPError as e:
+                    res[name] = {"unavailable": str(e)[:160]}
+                    continue
+                t = statistics.median(ts)
+                ach = workload_units(cfg) * UPDATE_BYTES[name] / t / 1e9
+                res[name] = {"value": workload_units(cfg) / t, "unit": UNIT, "ms_per_iter": t * 1e3,
+                             "ms_per_iter_min_max": [min(ts) * 1e3, max(ts) * 1e3],
+                             "roofline": {"bound": "hbm", "bytes_per_update": UPDATE_BYTES[name], "achieved": ach,
+                                          "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                                          "peak_source": pk["source"]}}
+        res["clocks"] = clk.summary()
+        if "value" in res.get("band_mM", {}) and "value" in res.get("dense_bf16_tcgen05_fused", {}):
+            res["band_over_fused_tcgen05"] = res["band_mM"]["value"] / res["dense_bf16_tcgen05_fused"]["value"]
         res["layout"] = list(bp.bp_get_layout(G.h))
         out[f"M{M}_T{T}"] = res
         G.close()
         del u
         torch.cuda.empty_cache()
-    line = {"metric": METRIC + " vs the O(M^2) baselines", "value": out["M64_T3"]["band_mM"]["value"], "unit": UNIT,
+    return out
+
+
+def run_dense_compare_workload(args):
+    out = measure_dense_compare(args)
+    first = next(iter(out.values()))
+    line = {"metric": METRIC + " vs the O(M^2) baselines", "value": first["band_mM"]["value"], "unit": UNIT,
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1280x720 random-dot stereo, synchronous sum-product, M = 64 (T = 3) and "
-                                   "M = 128 (T = 4); the O(M^2) updates run on the same grid and state"},
-            "peak_source": pk["source"], "modes": out}
+            "config": {"workload": "1280x720 random-dot stereo, synchronous sum-product, M = 64 (T = 3), "
+                                   "M = 128 (T = 4) and M = 256 (T = 4); the O(M^2) updates run on the same grid "
+                                   "and state"},
+            "peak_source": peaks()["source"], "modes": out}
     print(json.dumps(line))
 
 
@@ -1012,13 +1033,18 @@ def main():
     if not args.no_secondary and world == 1:
         # the other workloads of the hot path, each with its own roofline and
         # clocks: the 384x288 red-black grid (both modes), the 64-MRF batch
-        # (both modes) and the checkpointed gradient
+        # (both modes), the checkpointed gradient, and the O(mM) update
+        # against the tensor-core O(M^2) update at 256 labels
         sec_args = argparse.Namespace(**vars(args))
         sec_args.steps, sec_args.warmup = max(3, min(args.steps, 10)), max(3, min(args.warmup, 3))
         sec = {}
         for key, fn in (("grid384x288_m16", lambda: measure_grid(sec_args, "grid384x288_m16")),
                         ("batch64", lambda: measure_batch(sec_args)),
-                        ("grid256_m64_grad", lambda: measure_gradient(sec_args))):
+                        ("grid256_m64_grad", lambda: measure_gradient(sec_args)),
+                        ("dense_compare_m256", lambda: (measure_dense_compare(sec_args, ((256, 4),), cuda_core=False),
+                                                        {"workload": "1280x720, M = 256, T = 4, synchronous "
+                                                                     "sum-product: O(mM) band against the fused and "
+                                                                     "packed BF16 tcgen05 O(M^2) updates"}))):
             try:
                 r, c = fn()
                 sec[key] = {"config": c, "steps": sec_args.steps, "warmup": sec_args.warmup, "result": r}

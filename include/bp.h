@@ -73,10 +73,10 @@ typedef enum {
     BP_DENSE_CUDA_CORE = 0, /* FP32 sum-product or int32 min-sum, CUDA cores          */
     BP_DENSE_BF16_TC = 1,   /* sum-product as a (nodes*4 x M)(M x M) tcgen05 GEMM,    */
                             /* BF16 operands, FP32 accumulate, normalising epilogue;  */
-                            /* h rows packed to HBM by a separate kernel (M 33..128)  */
+                            /* h rows packed to HBM by a separate kernel (M 33..256)  */
     BP_DENSE_BF16_TC_FUSED = 2 /* the same GEMM with h formed on chip from one read  */
                             /* of the node's vectors (same HBM bytes as the O(mM)     */
-                            /* update; M 33..128)                                     */
+                            /* update; M 33..256)                                     */
 } bp_dense_kind;
 
 /* Create a handle for the pairwise MRF of Eq. 1 on an H x W 4-connected grid

@@ -35,7 +35,9 @@ def _one_step(W, Hh, M, T, alpha, seed, fused=False):
 
 @pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("W,Hh,M,T", [(9, 7, 128, 4), (13, 5, 64, 3), (11, 6, 100, 4), (200, 100, 128, 4),
-                                      (1, 37, 128, 2), (45, 1, 64, 2)])
+                                      (1, 37, 128, 2), (45, 1, 64, 2),
+                                      # 256 labels: the K-block ring kernels (88 tiles, a ragged tail; 200 -> 256)
+                                      (70, 40, 256, 8), (13, 9, 256, 4), (11, 6, 200, 6), (1, 41, 256, 3)])
 def test_one_iteration_within_bf16_bound(W, Hh, M, T, fused):
     err = _one_step(W, Hh, M, T, 0.5, seed=W * Hh + M, fused=fused)
     assert err <= TOL, f"max relative error {err:.4e} > {TOL:.4e}"
@@ -71,12 +73,13 @@ def test_unsupported_label_count_is_reported():
     G.close()
 
 
-def test_fused_and_packed_forms_agree_bit_for_bit():
+@pytest.mark.parametrize("M,T", [(128, 4), (256, 6)])
+def test_fused_and_packed_forms_agree_bit_for_bit(M, T):
     """Both forms round the same h to BF16 and run the same MMAs, so the
     messages agree exactly."""
     from paper_1010_0012_gb300 import bp
-    rng = np.random.default_rng(17)
-    W, Hh, M, T = 33, 21, 128, 4
+    rng = np.random.default_rng(17 + M)
+    W, Hh = 33, 21
     g = rng.uniform(0.05, 1.0, (Hh, W, M)).astype(np.float32)
     p0 = H.random_planes_sum(W, Hh, M, rng)
     tab, fbar = wl.pair_table_f32(0.5, T)
