@@ -478,7 +478,9 @@ def measure_batch(args, n=64, K=30):
         b = bp.bp_batch_create(descs, dtype, stream=stream)
         del keep
         tune_ms = bp.bp_batch_autotune(b, mode, 8)
-        tiling = bp.bp_batch_get_tiling(b)
+        tiling = {"dominant_class": bp.bp_batch_get_tiling(b),
+                  "per_class (Mp, T, family, tile_words)": [bp.bp_batch_get_class_tiling(b, k)
+                                                            for k in range(bp.bp_batch_class_count(b))]}
 
         def step():
             bp.bp_batch_reset_messages(b)

@@ -302,13 +302,29 @@ bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode);
  * bp_get_messages) of MRF k; BP_ERR_ARG for k outside [0, n). */
 bp_status bp_batch_beliefs(bp_batch b, int k, void *dev_out, int32_t *dev_map);
 bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes);
-/* Work decomposition (no counterpart in the paper; results do not depend on
- * it): family 1 (4 labels per lane, C = 1) or 2 (8 labels per lane) and the
- * item size in label words.  bp_batch_autotune times every
- * candidate on this batch, keeps the fastest (cached in $BP_AUTOTUNE_CACHE when
- * set) and resets the messages. */
+/* Work decomposition (no counterpart in the paper; min-sum results do not
+ * depend on it, sum-product results only through the order of the terms of
+ * each sum): per (padded label count Mp, effective band half-width T) class
+ * of the batch, the lane layout (family 1: 4 labels per lane; 2: 8 labels per
+ * lane) and the item size in label words (256 .. 2^24).  One launch can mix
+ * classes of different families.
+ * bp_batch_set_tiling sets every class; bp_batch_get_tiling reports the
+ * setting of the class holding the most label words.  bp_batch_class_count
+ * returns the number of classes (-1 for NULL); bp_batch_get_class_tiling
+ * reports class k (classes in increasing (Mp, T) order; BP_ERR_ARG outside
+ * [0, count)); bp_batch_set_class_tiling sets the class (Mp, T) (BP_ERR_ARG if
+ * no MRF of the batch has it).
+ * bp_batch_autotune times, class by class, every (family, tile) candidate on
+ * that class's items alone for n_iters iterations, keeps each class's fastest,
+ * then times the whole batch with those choices: *host_best_ms (nullable) is
+ * that time per iteration.  The choices are cached in $BP_AUTOTUNE_CACHE when
+ * set (a second call on a batch of the same classes and size reads them).
+ * Resets the messages. */
 bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words);
 bp_status bp_batch_get_tiling(bp_batch b, int *family, int *tile_words);
+int bp_batch_class_count(bp_batch b);
+bp_status bp_batch_get_class_tiling(bp_batch b, int k, int *Mp, int *T, int *family, int *tile_words);
+bp_status bp_batch_set_class_tiling(bp_batch b, int Mp, int T, int family, int tile_words);
 bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms);
 /* Bound of the grid-barrier wait (default 2 s; failure detection, no
  * counterpart in the paper).  extra_arrivals = 1 makes the

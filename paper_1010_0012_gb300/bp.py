@@ -76,6 +76,9 @@ def _load():
         "bp_batch_get_messages": ([P, I, P], I),
         "bp_batch_set_tiling": ([P, I, I], I),
         "bp_batch_get_tiling": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+        "bp_batch_class_count": ([P], I),
+        "bp_batch_get_class_tiling": ([P, I, P, P, P, P], I),
+        "bp_batch_set_class_tiling": ([P, I, I, I, I], I),
         "bp_batch_autotune": ([P, I, I, ctypes.POINTER(ctypes.c_float)], I),
         "bp_batch_set_wait_limit": ([P, D, I], I),
         "bp_batch_sync": ([P], I),
@@ -384,6 +387,21 @@ def bp_batch_get_tiling(b):
     f, t = ctypes.c_int(), ctypes.c_int()
     _bcheck(b, _lib.bp_batch_get_tiling(b, ctypes.byref(f), ctypes.byref(t)))
     return f.value, t.value
+
+
+def bp_batch_class_count(b):
+    return _lib.bp_batch_class_count(b)
+
+
+def bp_batch_get_class_tiling(b, k):
+    """(Mp, T, family, tile_words) of class k."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _bcheck(b, _lib.bp_batch_get_class_tiling(b, int(k), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def bp_batch_set_class_tiling(b, Mp, T, family, tile_words):
+    _bcheck(b, _lib.bp_batch_set_class_tiling(b, int(Mp), int(T), int(family), int(tile_words)))
 
 
 def bp_batch_autotune(b, mode, n_iters=3):

@@ -162,6 +162,21 @@ __device__ __forceinline__ void batch_dispatch(const BatchMrf *__restrict__ m, i
     }
 }
 
+// FAM = 0: each item runs the family of its MRF's class (classes with
+// different lane layouts in one launch)
+template <int FAM, bool MIN, bool RB, bool FULL>
+__device__ __forceinline__ void batch_dispatch_any(const BatchMrf *__restrict__ m, int node0, int count, int src,
+                                                   int parity) {
+    if constexpr (FAM == 0) {
+        if (m->family == 2)
+            batch_dispatch<2, MIN, RB, FULL>(m, node0, count, src, parity);
+        else
+            batch_dispatch<1, MIN, RB, FULL>(m, node0, count, src, parity);
+    } else {
+        batch_dispatch<FAM, MIN, RB, FULL>(m, node0, count, src, parity);
+    }
+}
+
 // RB: the red-black form (two in-place half-steps per iteration), compiled
 // separately so that the synchronous batch kernel keeps its registers.
 template <int FAM, bool MIN, bool RB, bool FULL = false>
@@ -183,7 +198,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs a) {
         while (ticket < first + n_items) {
             if (threadIdx.x == 0) s_ticket[slot ^ 1] = atomicAdd(a.tickets, 1ull);
             const BatchItem item = a.items[ticket - first];
-            batch_dispatch<FAM, MIN, RB, FULL>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
+            batch_dispatch_any<FAM, MIN, RB, FULL>(a.mrfs + item.mrf, item.node0, item.count, src, parity);
             __syncthreads();
             slot ^= 1;
             ticket = s_ticket[slot];

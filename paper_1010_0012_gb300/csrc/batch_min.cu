@@ -9,11 +9,14 @@ const void *batch_min_kernel_f2();        // batch_min_f2.cu
 const void *batch_min_kernel_f1_full();   // batch_min_f1_full.cu
 const void *batch_min_kernel_f2_full();   // batch_min_f2_full.cu
 const void *batch_min_kernel_rb();        // batch_min_rb.cu
+const void *batch_min_kernel_mixed();     // batch_min_mixed.cu
+const void *batch_min_kernel_mixed_full();   // batch_min_mixed_full.cu
 
 // full: every MRF has M == Mp, the variant without padded-label masks (same
 // launch bounds, so the same two resident blocks per SM)
 static const void *batch_min_fn(int family, bool redblack = false, bool full = false) {
     if (redblack) return batch_min_kernel_rb();
+    if (family == 0) return full ? batch_min_kernel_mixed_full() : batch_min_kernel_mixed();
     if (full) return family == 2 ? batch_min_kernel_f2_full() : batch_min_kernel_f1_full();
     return family == 2 ? batch_min_kernel_f2() : batch_min_kernel_f1();
 }

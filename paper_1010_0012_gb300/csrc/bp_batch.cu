@@ -45,9 +45,9 @@ struct MrfHost {
 };
 
 struct BatchGraphKey {
-    int n, mode, cur, family, tile, blocks;
+    int n, mode, cur, family, gen, blocks;
     bool operator<(const BatchGraphKey &o) const {
-        return std::tie(n, mode, cur, family, tile, blocks) < std::tie(o.n, o.mode, o.cur, o.family, o.tile, o.blocks);
+        return std::tie(n, mode, cur, family, gen, blocks) < std::tie(o.n, o.mode, o.cur, o.family, o.gen, o.blocks);
     }
 };
 
@@ -67,10 +67,13 @@ struct bp_batch_ctx {
     int n_items = 0, items_cap = 0;
     unsigned *d_bar = nullptr;   // barrier and work-counter words (kBatchCtlWords)
     int *d_status = nullptr;
-    int family = 1;
-    int tile_words = 16384;
+    int family = 1;              // lane layout of the launch: 1 or 2 for every MRF, 0 when classes differ
+    // work decomposition per (Mp, effective T) class: (family, item size in label words)
+    std::map<std::pair<int, int>, std::pair<int, int>> class_cfg;
+    std::vector<BatchMrf> dm;    // host copy of the device descriptors
     bool all_full = false;       // every MRF has M == Mp
-    int items_family = 0, items_tile = 0;
+    bool items_dirty = true;
+    int cfg_gen = 0;             // bumped at every rebuild of the items (graphs are keyed by it)
     int cur = 0;
     bool uniform_pending = true;
     bool use_graphs = true;
@@ -99,10 +102,31 @@ static void clear_batch_graphs(bp_batch b) {
     b->graphs.clear();
 }
 
-// Cut every MRF into items of about `tile_words` label words, whole groups of
-// nodes, listed class by class: widest band first, then most labels (one
-// compiled variant of the kernel per class).
-static bp_status build_items(bp_batch b) {
+static std::pair<int, int> class_of(const MrfHost &m) { return {m.Mp, m.Teff}; }
+
+// Install each class's lane layout in the device descriptors; the launch
+// family is that layout when every class shares it, else 0 (per MRF).
+static bp_status apply_class_cfg(bp_batch b) {
+    int fam = -1;
+    for (int k = 0; k < b->n; ++k) {
+        const int f = b->class_cfg[class_of(b->mrfs[k])].first;
+        b->dm[k].family = f;
+        fam = fam < 0 || fam == f ? f : 0;
+    }
+    b->family = fam < 0 ? 1 : fam;
+    BB_CK(b, cudaMemcpyAsync(b->d_mrfs, b->dm.data(), b->n * sizeof(BatchMrf), cudaMemcpyHostToDevice, b->stream));
+    BB_CK(b, cudaStreamSynchronize(b->stream));
+    b->items_dirty = true;
+    return BP_OK;
+}
+
+// Cut every MRF into items of about its class's item size in label words,
+// whole groups of nodes, listed class by class: widest band first, then most
+// labels (one compiled variant of the kernel per class).  only: restrict to
+// that class (the autotuner times classes alone).  Cached graphs hold the
+// item list's address and count, so they are dropped.
+static bp_status build_items(bp_batch b, const std::pair<int, int> *only = nullptr) {
+    clear_batch_graphs(b);
     std::vector<int> order(b->n);
     for (int k = 0; k < b->n; ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -112,23 +136,27 @@ static bp_status build_items(bp_batch b) {
     std::vector<BatchItem> items;
     for (int k : order) {
         const MrfHost &m = b->mrfs[k];
-        const int gpb = kBlock / batch_lanes_per_node(b->family, m.Mp);
-        int tile = std::max(gpb, (b->tile_words / m.Mp) / gpb * gpb);
+        if (only && class_of(m) != *only) continue;
+        const std::pair<int, int> cfg = b->class_cfg[class_of(m)];
+        const int gpb = kBlock / batch_lanes_per_node(cfg.first, m.Mp);
+        int tile = std::max(gpb, (cfg.second / m.Mp) / gpb * gpb);
         const int N = m.W * m.H;
         for (int n0 = 0; n0 < N; n0 += tile) items.push_back(BatchItem{k, n0, std::min(tile, N - n0)});
     }
     if ((int)items.size() > b->items_cap) {
         if (b->d_items) cudaFree(b->d_items);
         b->d_items = nullptr;
+        b->items_cap = 0;
         BB_CK(b, cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
         b->items_cap = (int)items.size();
     }
-    BB_CK(b, cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
-                             b->stream));
+    if (!items.empty())
+        BB_CK(b, cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice,
+                                 b->stream));
     BB_CK(b, cudaStreamSynchronize(b->stream));
     b->n_items = (int)items.size();
-    b->items_family = b->family;
-    b->items_tile = b->tile_words;
+    b->items_dirty = only != nullptr;   // a one-class list is not the batch's
+    ++b->cfg_gen;
     return BP_OK;
 }
 
@@ -306,8 +334,13 @@ bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void 
     }
     if (st == BP_OK) {
         b->all_full = true;
-        for (const MrfHost &m : b->mrfs) b->all_full = b->all_full && m.M == m.Mp;
-        st = build_items(b);
+        for (const MrfHost &m : b->mrfs) {
+            b->all_full = b->all_full && m.M == m.Mp;
+            b->class_cfg[class_of(m)] = {1, 16384};   // until tuned: one chunk per lane, 16 K-word items
+        }
+        b->dm = dm;
+        st = apply_class_cfg(b);
+        if (!st) st = build_items(b);
         if (st) g_batch_err = b->err;
     }
     if (st != BP_OK) {
@@ -325,21 +358,59 @@ bp_status bp_batch_reset_messages(bp_batch b) {
     return BP_OK;
 }
 
+static bool tiling_ok(int family, int tile_words) {
+    return (family == 1 || family == 2) && tile_words >= 256 && tile_words <= (1 << 24);
+}
+
 bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words) {
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_set_tiling: NULL batch");
     b->err.clear();
-    if (family != 1 && family != 2) return bfail(b, BP_ERR_ARG, "bp_batch_set_tiling: family must be 1 or 2");
-    if (tile_words < 256 || tile_words > (1 << 24)) return bfail(b, BP_ERR_ARG, "bp_batch_set_tiling: tile out of range");
-    b->family = family;
-    b->tile_words = tile_words;
+    if (!tiling_ok(family, tile_words))
+        return bfail(b, BP_ERR_ARG, "bp_batch_set_tiling: family must be 1 or 2 and the tile in [256, 2^24] words");
+    for (auto &kv : b->class_cfg) kv.second = {family, tile_words};
+    if (bp_status st = apply_class_cfg(b)) return st;
     return build_items(b);
 }
 
+// the setting of the class holding the most label words
 bp_status bp_batch_get_tiling(bp_batch b, int *family, int *tile_words) {
     if (!b || !family || !tile_words) return bfail(b, BP_ERR_ARG, "bp_batch_get_tiling: NULL argument");
-    *family = b->family;
-    *tile_words = b->tile_words;
+    std::map<std::pair<int, int>, long long> words;
+    for (const MrfHost &m : b->mrfs) words[class_of(m)] += (long long)m.W * m.H * m.Mp;
+    auto best = words.begin();
+    for (auto it = words.begin(); it != words.end(); ++it)
+        if (it->second > best->second) best = it;
+    *family = b->class_cfg[best->first].first;
+    *tile_words = b->class_cfg[best->first].second;
     return BP_OK;
+}
+
+int bp_batch_class_count(bp_batch b) { return b ? (int)b->class_cfg.size() : -1; }
+
+bp_status bp_batch_get_class_tiling(bp_batch b, int k, int *Mp, int *T, int *family, int *tile_words) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_get_class_tiling: NULL batch");
+    b->err.clear();
+    if (!Mp || !T || !family || !tile_words) return bfail(b, BP_ERR_ARG, "bp_batch_get_class_tiling: NULL argument");
+    if (k < 0 || k >= (int)b->class_cfg.size()) return bfail(b, BP_ERR_ARG, "bp_batch_get_class_tiling: no class k");
+    auto it = b->class_cfg.begin();
+    std::advance(it, k);
+    *Mp = it->first.first;
+    *T = it->first.second;
+    *family = it->second.first;
+    *tile_words = it->second.second;
+    return BP_OK;
+}
+
+bp_status bp_batch_set_class_tiling(bp_batch b, int Mp, int T, int family, int tile_words) {
+    if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_set_class_tiling: NULL batch");
+    b->err.clear();
+    auto it = b->class_cfg.find({Mp, T});
+    if (it == b->class_cfg.end()) return bfail(b, BP_ERR_ARG, "bp_batch_set_class_tiling: no MRF has that (Mp, T)");
+    if (!tiling_ok(family, tile_words))
+        return bfail(b, BP_ERR_ARG, "bp_batch_set_class_tiling: family must be 1 or 2 and the tile in [256, 2^24] words");
+    it->second = {family, tile_words};
+    if (bp_status st = apply_class_cfg(b)) return st;
+    return build_items(b);
 }
 
 bp_status bp_batch_set_wait_limit(bp_batch b, double seconds, int extra_arrivals) {
@@ -361,13 +432,13 @@ bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode) {
         return bfail(b, BP_ERR_ARG, "bp_batch_iterate: BP_SUM needs BP_F32, BP_MAX needs BP_I32");
     if (bp_status st = materialize_batch(b)) return st;
     if (n_iters == 0) return BP_OK;
-    if (b->items_family != b->family || b->items_tile != b->tile_words)
+    if (b->items_dirty)
         if (bp_status st = build_items(b)) return st;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     BB_CK(b, cudaStreamIsCapturing(b->stream, &cap));
     const int end_cur = (b->cur + n_iters) & 1;
     if (b->use_graphs && cap == cudaStreamCaptureStatusNone) {
-        const BatchGraphKey key{n_iters, mode, b->cur, b->family, b->tile_words, batch_blocks(b)};
+        const BatchGraphKey key{n_iters, mode, b->cur, b->family, b->cfg_gen, batch_blocks(b)};
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             cudaGraph_t g = nullptr;
@@ -441,68 +512,109 @@ bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes) {
     return BP_OK;
 }
 
-// Project-written autotuner: times every (family, tile) candidate on this
-// batch for n_iters iterations (after one warm-up run each), keeps the
-// fastest, and records it in a cache file keyed by the batch's (Mp, T)
-// classes and size (path: $BP_AUTOTUNE_CACHE, if set).  Leaves the messages
-// reset to the uniform state.
+// Project-written autotuner, per (Mp, T) class: every (family, tile)
+// candidate runs the class's items alone for n_iters iterations (after one
+// warm-up run) on the kernel compiled for that family; the fastest is kept for
+// the class.  Then the whole batch runs with every class's choice, and that
+// time per iteration is returned.  The choices are recorded in a cache file
+// keyed by the batch's classes and size (path: $BP_AUTOTUNE_CACHE, if set).
+// Leaves the messages reset to the uniform state.
 bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms) {
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_autotune: NULL batch");
     b->err.clear();
     if (n_iters < 1) return bfail(b, BP_ERR_ARG, "bp_batch_autotune: n_iters < 1");
+    if ((mode == BP_MAX) != (b->dtype == BP_I32) || (mode != BP_SUM && mode != BP_MAX))
+        return bfail(b, BP_ERR_ARG, "bp_batch_autotune: BP_SUM needs BP_F32, BP_MAX needs BP_I32");
     std::ostringstream sig;
     long long words = 0;
     std::map<std::pair<int, int>, long long> classes;
     for (auto &m : b->mrfs) {
-        classes[{m.Mp, m.Teff}] += (long long)m.W * m.H;
+        classes[class_of(m)] += (long long)m.W * m.H;
         words += (long long)m.W * m.H * m.Mp;
     }
     sig << (b->dtype == BP_I32 ? "i32" : "f32") << ":m" << mode << ":w" << (int)std::log2((double)words + 1);
     for (auto &kv : classes) sig << ":" << kv.first.first << "x" << kv.first.second;
     const char *cache = std::getenv("BP_AUTOTUNE_CACHE");
     if (cache) {
+        // line: signature, class count, then (Mp, T, family, tile) per class, then ms per iteration
         std::ifstream in(cache);
-        std::string key;
-        int fam, tile;
-        float ms;
-        while (in >> key >> fam >> tile >> ms)
-            if (key == sig.str()) {
-                if (bp_status st = bp_batch_set_tiling(b, fam, tile)) return st;
-                if (host_best_ms) *host_best_ms = ms;
-                return bp_batch_reset_messages(b);
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string key;
+            int nc = 0;
+            if (!(ls >> key >> nc) || key != sig.str() || nc != (int)b->class_cfg.size()) continue;
+            std::map<std::pair<int, int>, std::pair<int, int>> cfg;
+            bool good = true;
+            for (int i = 0; i < nc && good; ++i) {
+                int mp, t, f, tile;
+                good = (bool)(ls >> mp >> t >> f >> tile) && b->class_cfg.count({mp, t}) && tiling_ok(f, tile);
+                if (good) cfg[{mp, t}] = {f, tile};
             }
+            float ms = 0.f;
+            if (!good || !(ls >> ms) || (int)cfg.size() != nc) continue;
+            b->class_cfg = cfg;
+            if (bp_status st = apply_class_cfg(b)) return st;
+            if (bp_status st = build_items(b)) return st;
+            if (host_best_ms) *host_best_ms = ms;
+            return bp_batch_reset_messages(b);
+        }
     }
     const int fams[] = {1, 2};
     const int tiles[] = {16384, 65536, 262144};
     cudaEvent_t e0, e1;
     BB_CK(b, cudaEventCreate(&e0));
     BB_CK(b, cudaEventCreate(&e1));
-    float best = 3e38f;
-    int best_f = b->family, best_t = b->tile_words;
-    bp_status st = BP_OK;
-    for (int f : fams)
-        for (int t : tiles) {
-            if (st) break;
-            st = bp_batch_set_tiling(b, f, t);
-            if (!st) st = bp_batch_reset_messages(b);
-            if (!st) st = bp_batch_iterate(b, n_iters, mode);   // warm-up (and graph capture)
-            if (!st && cudaEventRecord(e0, b->stream) != cudaSuccess) st = BP_ERR_CUDA;
-            if (!st) st = bp_batch_iterate(b, n_iters, mode);
-            if (!st && cudaEventRecord(e1, b->stream) != cudaSuccess) st = BP_ERR_CUDA;
-            if (!st) st = bp_batch_sync(b);
-            float ms = 0.f;
-            if (!st) cudaEventElapsedTime(&ms, e0, e1);
-            if (!st && ms < best) { best = ms; best_f = f; best_t = t; }
-        }
+    bp_status st = materialize_batch(b);
+    auto timed = [&](auto &&run, float *ms) -> bp_status {
+        bp_status r = run();   // warm-up
+        if (!r && cudaEventRecord(e0, b->stream) != cudaSuccess) r = BP_ERR_CUDA;
+        if (!r) r = run();
+        if (!r && cudaEventRecord(e1, b->stream) != cudaSuccess) r = BP_ERR_CUDA;
+        if (!r) r = bp_batch_sync(b);
+        if (!r && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) r = BP_ERR_CUDA;
+        return r;
+    };
+    for (auto &kv : classes) {
+        if (st) break;
+        const std::pair<int, int> c = kv.first;
+        float best = 3e38f;
+        std::pair<int, int> best_cfg = b->class_cfg[c];
+        for (int f : fams)
+            for (int t : tiles) {
+                if (st) break;
+                b->class_cfg[c] = {f, t};
+                st = build_items(b, &c);
+                const int saved_family = b->family;
+                b->family = f;   // the class alone runs the kernel compiled for its family
+                float ms = 0.f;
+                if (!st)
+                    st = timed([&]() -> bp_status {
+                        return issue_batch(b, n_iters, b->cur) == cudaSuccess ? BP_OK : BP_ERR_CUDA;
+                    }, &ms);
+                b->family = saved_family;
+                if (!st && ms < best) {
+                    best = ms;
+                    best_cfg = {f, t};
+                }
+            }
+        b->class_cfg[c] = best_cfg;
+    }
+    float total = 0.f;
+    if (!st) st = apply_class_cfg(b);
+    if (!st) st = build_items(b);
+    if (!st) st = timed([&]() { return bp_batch_iterate(b, n_iters, mode); }, &total);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st == BP_ERR_CUDA ? bfail(b, st, "bp_batch_autotune: timing failed") : st;
-    if (bp_status s2 = bp_batch_set_tiling(b, best_f, best_t)) return s2;
     if (cache) {
         std::ofstream o(cache, std::ios::app);
-        o << sig.str() << " " << best_f << " " << best_t << " " << best / n_iters << "\n";
+        o << sig.str() << " " << b->class_cfg.size();
+        for (auto &kv : b->class_cfg)
+            o << " " << kv.first.first << " " << kv.first.second << " " << kv.second.first << " " << kv.second.second;
+        o << " " << total / n_iters << "\n";
     }
-    if (host_best_ms) *host_best_ms = best / n_iters;
+    if (host_best_ms) *host_best_ms = total / n_iters;
     return bp_batch_reset_messages(b);
 }
 

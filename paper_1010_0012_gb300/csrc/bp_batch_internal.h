@@ -21,6 +21,7 @@ struct BatchMrf {
     int32_t ebar;
     int zero_min;                   // 1 if E(0) is the table's minimum
     int packed16;                   // 1: min-sum band on 16-bit label pairs (see MinBand)
+    int family;                     // lane layout of this MRF's (Mp, T) class: 1 or 2 chunks per lane
 };
 
 // A run of `count` consecutive slots of one MRF: nodes for a synchronous
@@ -55,7 +56,8 @@ constexpr size_t kBatchZeroBytes = 16;
 constexpr int kBatchTicketWord = 2;
 constexpr int kBatchGenWord = 4;
 
-// Launch one persistent cooperative batch kernel (family 1 or 2).
+// Launch one persistent cooperative batch kernel (family 1 or 2 for every MRF,
+// or 0: each MRF's own family).
 cudaError_t launch_batch(const BatchArgs &a, int family, bool min_sum, int blocks, cudaStream_t s);
 // Largest co-resident grid for that kernel.
 int batch_max_blocks(int family, bool min_sum);

@@ -159,6 +159,67 @@ def test_barrier_time_out_is_reported_and_the_context_survives():
     bp.bp_batch_destroy(b)
 
 
+def H_padded(M):
+    mp = 16
+    while mp < M:
+        mp *= 2
+    return mp
+
+
+@pytest.mark.parametrize("dtype_name", ["i32", "f32"])
+def test_classes_with_different_lane_layouts_in_one_launch(dtype_name):
+    """Each (Mp, T) class on its own family and item size: the launch mixes
+    both lane layouts and stays exact (min-sum bit for bit, sum-product
+    within 1e-5 of the FP64 oracle)."""
+    import torch
+    from paper_1010_0012_gb300 import bp
+    mrfs = _mrfs(n=8, seed=21)
+    dtype = bp.BP_I32 if dtype_name == "i32" else bp.BP_F32
+    descs, keep = [], []
+    for cfg, st in mrfs:
+        if dtype == bp.BP_F32:
+            un = torch.from_numpy(wl.unary_f32(st)).cuda()
+            tab, fb = wl.pair_table_f32(cfg.alpha, cfg.T)
+        else:
+            un = torch.from_numpy(wl.unary_i32(st)).cuda()
+            tab, fb = wl.pair_table_i32(cfg.alpha, cfg.T)
+        keep.append(un)
+        descs.append((un, tab, cfg.T, fb))
+    b = bp.bp_batch_create(descs, dtype)
+    n = bp.bp_batch_class_count(b)
+    assert n >= 2
+    for k in range(n):
+        Mp, T, _, _ = bp.bp_batch_get_class_tiling(b, k)
+        bp.bp_batch_set_class_tiling(b, Mp, T, 1 + k % 2, 512 * (1 + k))
+    got = [bp.bp_batch_get_class_tiling(b, k) for k in range(n)]
+    assert [g[2:] for g in got] == [(1 + k % 2, 512 * (1 + k)) for k in range(n)]
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_batch_set_class_tiling(b, 48, 3, 1, 4096)
+    assert ei.value.status == bp.BP_ERR_ARG
+    with pytest.raises(bp.BPError) as ei:
+        bp.bp_batch_get_class_tiling(b, n)
+    assert ei.value.status == bp.BP_ERR_ARG
+    bp.bp_batch_reset_messages(b)
+    bp.bp_batch_iterate(b, 3, bp.BP_MAX if dtype == bp.BP_I32 else bp.BP_SUM)
+    bp.bp_batch_iterate(b, 3, bp.BP_MAX if dtype == bp.BP_I32 else bp.BP_SUM)
+    res = []
+    for k, (cfg, st) in enumerate(mrfs):
+        bel = torch.empty((cfg.H, cfg.W, cfg.M), dtype=torch.float32 if dtype == bp.BP_F32 else torch.int32,
+                          device="cuda")
+        mp = torch.empty((cfg.H, cfg.W), dtype=torch.int32, device="cuda")
+        pl = torch.empty((4, cfg.H, cfg.W, cfg.M), dtype=bel.dtype, device="cuda")
+        bp.bp_batch_beliefs(b, k, bel, mp)
+        bp.bp_batch_get_messages(b, k, pl)
+        res.append((bel, mp, pl))
+    bp.bp_batch_sync(b)
+    res = [(x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy()) for x, y, z in res]
+    bp.bp_batch_destroy(b)
+    if dtype == bp.BP_I32:
+        _check_min(mrfs, res, 6)
+    else:
+        _check_sum(mrfs, res, 6)
+
+
 def test_autotune_picks_a_candidate_and_stays_exact(tmp_path, monkeypatch):
     import torch
     from paper_1010_0012_gb300 import bp
@@ -173,7 +234,11 @@ def test_autotune_picks_a_candidate_and_stays_exact(tmp_path, monkeypatch):
     ms = bp.bp_batch_autotune(b, bp.BP_MAX, 2)
     assert ms > 0
     fam, tile = bp.bp_batch_get_tiling(b)
-    assert fam in (1, 2) and tile in (4096, 16384, 65536)
+    assert fam in (1, 2) and tile in (16384, 65536, 262144)
+    classes = [bp.bp_batch_get_class_tiling(b, k) for k in range(bp.bp_batch_class_count(b))]
+    want = sorted({(H_padded(cfg.M), min(cfg.T, cfg.M - 1)) for cfg, st in mrfs})
+    assert [c[:2] for c in classes] == want
+    assert all(f in (1, 2) and t in (16384, 65536, 262144) for _, _, f, t in classes)
     assert (tmp_path / "tune.txt").read_text().strip()
     bp.bp_batch_iterate(b, 5, bp.BP_MAX)
     bp.bp_batch_sync(b)
@@ -189,6 +254,7 @@ def test_autotune_picks_a_candidate_and_stays_exact(tmp_path, monkeypatch):
     b2 = bp.bp_batch_create(descs, bp.BP_I32)
     bp.bp_batch_autotune(b2, bp.BP_MAX, 2)
     assert bp.bp_batch_get_tiling(b2) == (fam, tile)
+    assert [bp.bp_batch_get_class_tiling(b2, k) for k in range(bp.bp_batch_class_count(b2))] == classes
     bp.bp_batch_destroy(b)
     bp.bp_batch_destroy(b2)
 
