@@ -315,9 +315,11 @@ bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes);
  * [0, count)); bp_batch_set_class_tiling sets the class (Mp, T) (BP_ERR_ARG if
  * no MRF of the batch has it).
  * bp_batch_autotune times, class by class, every (family, tile) candidate on
- * that class's items alone for n_iters iterations, keeps each class's fastest,
- * then times the whole batch with those choices: *host_best_ms (nullable) is
- * that time per iteration.  The choices are cached in $BP_AUTOTUNE_CACHE when
+ * that class's items alone for n_iters iterations and keeps each class's
+ * fastest; then it times the whole batch under those choices, under the same
+ * item sizes with one family for every class, and under each single setting
+ * for all classes, and keeps the fastest: *host_best_ms (nullable) is its
+ * time per iteration.  The choices are cached in $BP_AUTOTUNE_CACHE when
  * set (a second call on a batch of the same classes and size reads them).
  * Resets the messages. */
 bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words);

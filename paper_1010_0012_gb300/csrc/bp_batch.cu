@@ -515,8 +515,9 @@ bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes) {
 // Project-written autotuner, per (Mp, T) class: every (family, tile)
 // candidate runs the class's items alone for n_iters iterations (after one
 // warm-up run) on the kernel compiled for that family; the fastest is kept for
-// the class.  Then the whole batch runs with every class's choice, and that
-// time per iteration is returned.  The choices are recorded in a cache file
+// the class.  Then whole-batch candidates are timed: the per-class choices,
+// those item sizes with one lane layout for every class, and the uniform
+// settings; the fastest is kept and its time per iteration returned.  The choices are recorded in a cache file
 // keyed by the batch's classes and size (path: $BP_AUTOTUNE_CACHE, if set).
 // Leaves the messages reset to the uniform state.
 bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms) {
@@ -600,10 +601,39 @@ bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_
             }
         b->class_cfg[c] = best_cfg;
     }
-    float total = 0.f;
+    // whole-batch candidates: the per-class choices; the same item sizes with
+    // one lane layout for every class (one compiled family per launch is
+    // cheaper than a launch that switches layouts); one setting for all
+    std::vector<std::map<std::pair<int, int>, std::pair<int, int>>> cands;
+    cands.push_back(b->class_cfg);
+    for (int f : fams) {
+        auto c = b->class_cfg;
+        for (auto &kv : c) kv.second.first = f;
+        cands.push_back(c);
+    }
+    for (int f : fams)
+        for (int t : tiles) {
+            auto c = b->class_cfg;
+            for (auto &kv : c) kv.second = {f, t};
+            cands.push_back(c);
+        }
+    float total = 3e38f;
+    std::map<std::pair<int, int>, std::pair<int, int>> best_cfg = b->class_cfg;
+    for (const auto &c : cands) {
+        if (st) break;
+        b->class_cfg = c;
+        float ms = 0.f;
+        st = apply_class_cfg(b);
+        if (!st) st = build_items(b);
+        if (!st) st = timed([&]() { return bp_batch_iterate(b, n_iters, mode); }, &ms);
+        if (!st && ms < total) {
+            total = ms;
+            best_cfg = c;
+        }
+    }
+    b->class_cfg = best_cfg;
     if (!st) st = apply_class_cfg(b);
     if (!st) st = build_items(b);
-    if (!st) st = timed([&]() { return bp_batch_iterate(b, n_iters, mode); }, &total);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st == BP_ERR_CUDA ? bfail(b, st, "bp_batch_autotune: timing failed") : st;
