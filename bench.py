@@ -934,6 +934,23 @@ def run_factor_workload(args):
         res[name] = {"value": units * K / t, "unit": "factor-to-variable message entries/s",
                      "ms_per_iter": t * 1e3 / K}
     bp.bp_fg_destroy(G)
+    # roofline of the O(C + M) iteration: every triplet contributes one term to
+    # each of the three messages of every factor (n_factors * 3 * C terms per
+    # iteration); per 32 terms a warp spends four L1 / shared-memory data-pipe
+    # wavefronts (two 4-byte gathers of the incoming messages and the 8-byte
+    # entry read through L1), one wavefront per cycle per SM
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+    terms = len(fs) * 3 * len(trip)
+    t_it = res["sparse_O(C+M)"]["ms_per_iter"] / 1e3
+    peak_terms = props.multi_processor_count * sm_mhz * 1e6 * 32 / 4
+    res["sparse_O(C+M)"]["roofline"] = {
+        "bound": "alu", "resource": "L1 / shared-memory data pipe: 4 wavefronts per 32 triplet terms",
+        "achieved": terms / t_it / 1e9, "peak": peak_terms / 1e9, "unit": "G terms/s",
+        "frac": terms / t_it / peak_terms, "terms_per_iteration": terms,
+        "hbm_bytes_per_iteration": len(fs) * 6 * M * 4 + W * H * M * 4 * 2,
+        "hbm_frac": (len(fs) * 6 * M * 4 + W * H * M * 4 * 2) / t_it / (peaks()["hbm_gbs"] * 1e9)}
     line = {"metric": "factor BP message entries/s, O(C) vs O(M^3) (three-variable factors)",
             "value": res["sparse_O(C+M)"]["value"], "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
             "warmup": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",

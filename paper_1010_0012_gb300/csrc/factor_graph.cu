@@ -115,17 +115,29 @@ __global__ void v2f_kernel(const E *unary, const int32_t *var_ptr, const int32_t
 
 // ---- factor -> variable: the O(C + M) update -----------------------------------
 // The triplet list is held per slot s and output label x_s as a list of
-// (x_u | x_w << 16, weight bits), interleaved by label (entry i of label x at
-// base_s + i * M + x: consecutive lanes read consecutive words, through L1,
-// where the table stays) and sorted by the offsets (x_u - x_s, x_w - x_s) mod M,
-// so that at each step the lanes gather n_u and n_w from different banks of
-// the warp's shared-memory copy of the incoming messages.  One warp per factor;
-// lane l produces labels l, l + 32, ... (KM of them) and walks their lists side
-// by side.
+// (x_u | x_w << 16, weight bits), sorted by the offsets (x_u - x_s, x_w - x_s)
+// mod M so that lanes working on neighbouring labels gather n_u and n_w from
+// different banks of the warp's shared-memory copy of the incoming messages.
+// The lists are dealt to lanes in pairs (longest with shortest of the slot,
+// on lanes 2j and 2j + 1 of chunk k): the even lane takes the first half of
+// the pair's entries, all of the long list's; the odd lane the long list's
+// rest (its foreign entries, summed apart) and then its own short list.  One
+// shuffle returns the foreign partial to its owner.  A slot then costs about
+// its mean list length instead of its longest.  Entries are interleaved by
+// lane (step i of chunk k at i * 32 KM + 32 k + lane: consecutive lanes read
+// consecutive words, through L1, where the table stays).  One warp per
+// factor; no atomics.
+// chunks of 32 labels per lane of the compiled f2v kernels (1, 2, 4 or 8)
+inline int f2v_chunks(int Mp) {
+    const int km = (Mp + 31) / 32;
+    return km <= 1 ? 1 : km <= 2 ? 2 : km <= 4 ? 4 : 8;
+}
+
 struct FgTable {
-    const int2 *ell;        // [sum_s rows_s * M]
-    const int32_t *len;     // [3][M]
+    const int2 *ell;        // per slot: [rows_s][32 KM] entries
+    const int32_t *meta;    // [3][KM][32][3]: entry count, foreign count, own label (-1: none)
     long long base[3];      // start of slot s in ell
+    int rows[3];            // steps of slot s
 };
 
 template <bool MIN, typename E, int KM>
@@ -135,17 +147,6 @@ __global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, c
     const int M = d.M, Mp = d.Mp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     E *n = (E *)sm + warp * 3 * Mp;                       // [3][Mp] per warp
-    int len[3][KM], len_max[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        len_max[s] = 0;
-#pragma unroll
-        for (int k = 0; k < KM; ++k) {
-            const int x = lane + 32 * k;
-            len[s][k] = x < M ? tab.len[s * M + x] : 0;
-            len_max[s] = max(len_max[s], len[s][k]);
-        }
-    }
     const long long gw = (long long)blockIdx.x * kFgWarps + warp, nw = (long long)gridDim.x * kFgWarps;
     for (long long a = gw; a < d.n_factors; a += nw) {
         E red[3];
@@ -170,25 +171,42 @@ __global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, c
             const int u = s == 0 ? 1 : 0, w = s == 2 ? 1 : 2;   // the other two slots, in order
             const E *nu = n + u * Mp, *nwv = n + w * Mp;
             const E flat = MIN ? fbar_or_ebar + red[u] + red[w] : fbar_or_ebar * red[u] * red[w];
-            const int2 *ell = tab.ell + tab.base[s];
-            E acc[KM];
+            const int2 *ell = tab.ell + tab.base[s] + lane;
+            int cnt[KM], nx[KM], lab[KM];
+            E acc[KM], accx[KM];
 #pragma unroll
-            for (int k = 0; k < KM; ++k) acc[k] = MIN ? flat : E(0);
-            for (int i = 0; i < len_max[s]; ++i) {
+            for (int k = 0; k < KM; ++k) {
+                const int32_t *mt = tab.meta + (((long long)s * KM + k) * 32 + lane) * 3;
+                cnt[k] = __ldg(mt);
+                nx[k] = __ldg(mt + 1);
+                lab[k] = __ldg(mt + 2);
+                acc[k] = MIN ? flat : E(0);
+                accx[k] = MIN ? E(kBig) : E(0);
+            }
+            const int rows = tab.rows[s];
+            for (int i = 0; i < rows; ++i) {
 #pragma unroll
                 for (int k = 0; k < KM; ++k) {
-                    if (i < len[s][k]) {
-                        const int2 e = __ldg(ell + (long long)i * M + lane + 32 * k);
+                    if (i < cnt[k]) {
+                        const int2 e = __ldg(ell + (long long)i * (32 * KM) + 32 * k);
                         const E gu = nu[e.x & 0xffff], gwv = nwv[e.x >> 16];
-                        if (MIN) acc[k] = __viaddmin_s32(e.y, gu + gwv, acc[k]);
-                        else acc[k] = fmaf(__int_as_float(e.y), gu * gwv, acc[k]);
+                        if (i < nx[k]) {
+                            if (MIN) accx[k] = __viaddmin_s32(e.y, gu + gwv, accx[k]);
+                            else accx[k] = fmaf(__int_as_float(e.y), gu * gwv, accx[k]);
+                        } else {
+                            if (MIN) acc[k] = __viaddmin_s32(e.y, gu + gwv, acc[k]);
+                            else acc[k] = fmaf(__int_as_float(e.y), gu * gwv, acc[k]);
+                        }
                     }
                 }
             }
             E norm = MIN ? E(kBig) : E(0);
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
-                if (lane + 32 * k < M) {
+                // the partner lane's foreign entries belong to this lane's label
+                const E o = __shfl_xor_sync(0xffffffffu, accx[k], 1);
+                if (MIN) acc[k] = o < acc[k] ? o : acc[k]; else acc[k] += o;
+                if (lab[k] >= 0 && lab[k] < M) {
                     if (!MIN) acc[k] += flat;
                     if (MIN) norm = acc[k] < norm ? acc[k] : norm; else norm += acc[k];
                 }
@@ -199,8 +217,8 @@ __global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, c
             }
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
-                const int x = lane + 32 * k;
-                if (x < Mp) {
+                const int x = lab[k];
+                if (x >= 0) {
                     E v;
                     if (MIN) v = x < M ? acc[k] - norm : E(0);
                     else v = x < M ? acc[k] / norm : E(0);
@@ -336,9 +354,10 @@ struct bp_fg_ctx {
     void *unary = nullptr;
     int32_t *var_ptr = nullptr, *var_inc = nullptr;
     void *m_fv = nullptr, *n_vf = nullptr;
-    int32_t *d_len = nullptr;   // [3][M] list lengths
+    int32_t *d_len = nullptr;   // [3][KM][32][3] per lane: entry count, foreign count, own label
     int2 *d_ell = nullptr;      // interleaved triplet lists (FgTable)
     long long ell_base[3] = {0, 0, 0};
+    int ell_rows[3] = {0, 0, 0};   // loop steps per slot
     void *d_dense = nullptr;
     int C = 0;
     double fbar = 0;
@@ -522,25 +541,58 @@ bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplet
             lists[(size_t)s * M + t[s]].push_back({{key_u, key_w}, make_int2(t[u] | (t[w] << 16), wbits[c])});
         }
     }
-    std::vector<int32_t> len((size_t)3 * M);
+    // Balance: per slot, the labels (padded to 32 KM lanes) sorted by list
+    // length and paired longest with shortest on the lanes 2j, 2j + 1 of one
+    // chunk k.  The pair's two lists are cut in half: the even lane takes the
+    // first h entries of the long list, the odd lane the rest of it (its
+    // "foreign" entries, into a second accumulator) and then the whole short
+    // list.  A slot's loop then runs about its mean list length instead of
+    // its longest.  Per (slot, chunk, lane): entry count, foreign count, own
+    // label (-1: none).
+    const int KM = f2v_chunks(g->Mp), L = 32 * KM;   // the compiled kernel's chunks
+    std::vector<int32_t> meta((size_t)3 * L * 3, 0);
+    std::vector<std::vector<int2>> lane_list((size_t)3 * L);
     long long base[3], total = 0;
+    int rows_s[3];
     for (int s = 0; s < 3; ++s) {
-        int rows = 0;
         for (int x = 0; x < M; ++x) {
             auto &l = lists[(size_t)s * M + x];
             std::stable_sort(l.begin(), l.end(), [](const auto &p, const auto &q) { return p.first < q.first; });
-            len[(size_t)s * M + x] = (int32_t)l.size();
-            rows = std::max(rows, (int)l.size());
         }
+        std::vector<int> order(L);
+        for (int x = 0; x < L; ++x) order[x] = x;
+        auto lenof = [&](int x) { return x < M ? (int)lists[(size_t)s * M + x].size() : 0; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lenof(a) > lenof(b); });
+        int rows = 0;
+        for (int j = 0; j < L / 2; ++j) {
+            const int A = order[j], B = order[L - 1 - j];
+            const int la = lenof(A), lb = lenof(B), h = (la + lb + 1) / 2;
+            const int k = j / 16, le = 2 * (j % 16), lo = le + 1;
+            const size_t pe = ((size_t)s * KM + k) * 32 + le, po = ((size_t)s * KM + k) * 32 + lo;
+            auto &ve = lane_list[pe], &vo = lane_list[po];
+            for (int i = 0; i < la; ++i) (i < h ? ve : vo).push_back(lists[(size_t)s * M + A][i].second);
+            const int nx = (int)vo.size();
+            for (int i = 0; i < lb; ++i) vo.push_back(lists[(size_t)s * M + B][i].second);
+            meta[pe * 3 + 0] = (int)ve.size();
+            meta[pe * 3 + 1] = 0;
+            meta[pe * 3 + 2] = A < g->Mp ? A : -1;
+            meta[po * 3 + 0] = (int)vo.size();
+            meta[po * 3 + 1] = nx;
+            meta[po * 3 + 2] = B < g->Mp ? B : -1;
+            rows = std::max(rows, (int)std::max(ve.size(), vo.size()));
+        }
+        rows_s[s] = rows;
         base[s] = total;
-        total += (long long)rows * M;
+        total += (long long)rows * L;
     }
     std::vector<int2> ell((size_t)std::max(1LL, total), make_int2(0, 0));
     for (int s = 0; s < 3; ++s)
-        for (int x = 0; x < M; ++x) {
-            const auto &l = lists[(size_t)s * M + x];
-            for (size_t i = 0; i < l.size(); ++i) ell[(size_t)(base[s] + (long long)i * M + x)] = l[i].second;
-        }
+        for (int k = 0; k < KM; ++k)
+            for (int l = 0; l < 32; ++l) {
+                const auto &v = lane_list[((size_t)s * KM + k) * 32 + l];
+                for (size_t i = 0; i < v.size(); ++i) ell[(size_t)(base[s] + (long long)i * L + k * 32 + l)] = v[i];
+            }
+    std::vector<int32_t> &len = meta;   // uploaded as the per-lane table
     if (g->d_len) cudaFree(g->d_len);
     if (g->d_ell) cudaFree(g->d_ell);
     if (g->d_dense) cudaFree(g->d_dense);
@@ -549,7 +601,10 @@ bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplet
     FG_CK(g, cudaMalloc(&g->d_ell, ell.size() * sizeof(int2)));
     FG_CK(g, cudaMemcpy(g->d_len, len.data(), len.size() * 4, cudaMemcpyHostToDevice));
     FG_CK(g, cudaMemcpy(g->d_ell, ell.data(), ell.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    for (int s = 0; s < 3; ++s) g->ell_base[s] = base[s];
+    for (int s = 0; s < 3; ++s) {
+        g->ell_base[s] = base[s];
+        g->ell_rows[s] = rows_s[s];
+    }
     g->C = C;
     g->fbar = fbar;
     g->have_factor = true;
@@ -605,10 +660,11 @@ bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode) {
     if (bp_status st = fg_prepare(g, mode)) return st;
     if (g->n_factors == 0) return BP_OK;
     const FgDims d{g->n_vars, g->n_factors, g->M, g->Mp};
-    const FgTable tab{g->d_ell, g->d_len, {g->ell_base[0], g->ell_base[1], g->ell_base[2]}};
+    const FgTable tab{g->d_ell, g->d_len, {g->ell_base[0], g->ell_base[1], g->ell_base[2]},
+                      {g->ell_rows[0], g->ell_rows[1], g->ell_rows[2]}};
     for (int it = 0; it < n_iters; ++it) {
         if (bp_status st = fg_v2f(g)) return st;
-        const int km = (g->Mp + 31) / 32;
+        const int km = f2v_chunks(g->Mp);   // the table was built for this many chunks
         cudaError_t e = g->dtype == BP_F32
             ? (km <= 1 ? launch_f2v<false, float, 1>(g, tab, d) : km <= 2 ? launch_f2v<false, float, 2>(g, tab, d)
                : km <= 4 ? launch_f2v<false, float, 4>(g, tab, d) : launch_f2v<false, float, 8>(g, tab, d))

@@ -120,3 +120,44 @@ def test_factor_hub_variable_degrees(hub_degree):
     np.testing.assert_array_equal(msg.astype(np.int64), m64)
     np.testing.assert_array_equal(bel.astype(np.int64), b64)
     np.testing.assert_array_equal(mp, oracle.map_labels(b64, maximise=False))
+
+
+def second_difference_triplets(M, alpha=1.0):
+    """The benchmark's smoothness potential: f = exp(-alpha |x0 - 2 x1 + x2|)
+    where the second difference is at most 1.  Its middle slot's lists run
+    from 3 to ~3M entries, so the balanced deal splits long lists across lanes."""
+    x0, x1, x2 = np.meshgrid(np.arange(M), np.arange(M), np.arange(M), indexing="ij")
+    d2 = np.abs(x0 - 2 * x1 + x2)
+    keep = d2 <= 1
+    trip = np.stack([x0[keep], x1[keep], x2[keep]], 1).astype(np.int32)
+    return trip, d2[keep]
+
+
+@pytest.mark.parametrize("M", [32, 70])
+def test_factor_uneven_lists_sum_and_min_sum(M):
+    """Uneven lists (split across lane pairs) and, at M = 70, 3 chunks of 32
+    labels served by the 4-chunk kernel: sum-product within 1e-5 of the FP64
+    oracle, min-sum bit for bit."""
+    import oracle
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(M)
+    nv, nf = 30, 24
+    fs = random_graph(nv, nf, rng)
+    trip, d2 = second_difference_triplets(M)
+    vals = np.exp(-d2.astype(np.float64)).astype(np.float32)
+    fbar = float(np.float32(np.exp(-2.0)))
+    g = rng.uniform(0.05, 1.0, (nv, M)).astype(np.float32)
+    bel, mp, msg = _gpu(g, fs, trip, vals, fbar, 4, bp.BP_F32)
+    F = factor.dense_table(trip, vals.astype(np.float64), fbar, M)
+    m64, b64 = factor.sum_product(g.astype(np.float64), fs, F, 4)
+    assert H.node_rel_err(bel, b64) <= H.REL_TOL
+    assert float(np.max(np.abs(msg - m64).max(-1) / np.abs(m64).max(-1))) <= H.REL_TOL
+    E = rng.integers(0, 25, (nv, M)).astype(np.int32)
+    ebar = 4
+    vi = (2 * d2).astype(np.int32)
+    bel, mp, msg = _gpu(E, fs, trip, vi, ebar, 4, bp.BP_I32)
+    V = factor.dense_table(trip, vi.astype(np.int64), ebar, M, dtype=np.int64)
+    m64, b64 = factor.min_sum(E.astype(np.int64), fs, V, 4)
+    np.testing.assert_array_equal(msg.astype(np.int64), m64)
+    np.testing.assert_array_equal(bel.astype(np.int64), b64)
+    np.testing.assert_array_equal(mp, oracle.map_labels(b64, maximise=False))
