@@ -32,6 +32,12 @@
  *    errors are returned synchronously and nothing is launched; device
  *    errors and kernel time-outs surface at the next call or at bp_sync.
  *  - A handle is not thread-safe; use one handle per host thread.
+ *  - Tracing: the main calls (create, set, iterate, beliefs, backward, sync,
+ *    autotune, of single grids, batches and factor graphs) each open an NVTX
+ *    range named after the call.  With the environment variable BP_LOG set to
+ *    a value other than 0 when the first of them runs, each also writes one
+ *    line to stderr with its host-side time ("[bp] <call> <us> us host"), and
+ *    every error any call reports is written as "[bp] error <status>: <message>".
  */
 #ifndef BPGRID_BP_H
 #define BPGRID_BP_H

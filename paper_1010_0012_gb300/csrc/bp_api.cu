@@ -13,6 +13,7 @@
 #include <tuple>
 #include <vector>
 
+#include "trace.h"
 #include "../../include/bp.h"
 #include "bp_batch_internal.h"
 #include "bp_internal.h"
@@ -34,6 +35,7 @@ thread_local std::string g_global_err;
 
 bp_status fail(bp_ctx *h, bp_status st, const std::string &msg) {
     if (h) h->err = msg; else g_global_err = msg;
+    if (st != BP_OK) log_error(st, msg);
     return st;
 }
 
@@ -333,6 +335,7 @@ const char *bp_last_error(bp_handle h) { return h ? h->err.c_str() : g_global_er
 long long bp_launch_count(bp_handle h) { return h ? h->launches : -1; }
 
 bp_status bp_create(int W, int H, int M, bp_dtype dtype, void *cuda_stream, bp_handle *out) {
+    BPG_TRACE("bp_create");
     g_global_err.clear();
     if (!out) return fail(nullptr, BP_ERR_ARG, "bp_create: out is NULL");
     *out = nullptr;
@@ -406,6 +409,7 @@ void bp_destroy(bp_handle h) {
 }
 
 bp_status bp_set_unary(bp_handle h, const void *dev_unary) {
+    BPG_TRACE("bp_set_unary");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary: NULL handle");
     h->err.clear();
     if (!dev_unary) return fail(h, BP_ERR_ARG, "bp_set_unary: NULL unary");
@@ -424,6 +428,7 @@ bp_status bp_set_unary(bp_handle h, const void *dev_unary) {
 
 bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *left, const uint8_t *right,
                               const void *host_table, int Tu) {
+    BPG_TRACE("bp_set_unary_stereo");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary_stereo: NULL handle");
     h->err.clear();
     if (!left || !right || !host_table) return fail(h, BP_ERR_ARG, "bp_set_unary_stereo: NULL argument");
@@ -467,6 +472,7 @@ bp_status bp_set_unary_stereo(bp_handle h, const uint8_t *left, const uint8_t *r
 }
 
 bp_status bp_set_unary_log(bp_handle h, const float *dev_logg) {
+    BPG_TRACE("bp_set_unary_log");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_unary_log: NULL handle");
     h->err.clear();
     if (!dev_logg) return fail(h, BP_ERR_ARG, "bp_set_unary_log: NULL unary");
@@ -484,6 +490,7 @@ bp_status bp_set_unary_log(bp_handle h, const float *dev_logg) {
 }
 
 bp_status bp_set_potential(bp_handle h, const void *host_table, int T, double fbar) {
+    BPG_TRACE("bp_set_potential");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_potential: NULL handle");
     h->err.clear();
     if (!host_table) return fail(h, BP_ERR_ARG, "bp_set_potential: NULL table");
@@ -605,6 +612,7 @@ static std::vector<int> sparse_bank_order(int M, const int32_t *rowptr, const in
 
 bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const int32_t *host_cols,
                                   const void *host_vals, double fbar) {
+    BPG_TRACE("bp_set_potential_sparse");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_potential_sparse: NULL handle");
     h->err.clear();
     if (!host_rowptr || !host_vals || (!host_cols && host_rowptr[h->M] != 0))
@@ -713,6 +721,7 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
 }
 
 bp_status bp_reset_messages(bp_handle h) {
+    BPG_TRACE("bp_reset_messages");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_reset_messages: NULL handle");
     h->err.clear();
     h->msg_uniform = true;
@@ -743,6 +752,7 @@ bp_status bp_get_layout(bp_handle h, int *L, int *C) {
 }
 
 bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule) {
+    BPG_TRACE("bp_iterate");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_iterate: NULL handle");
     h->err.clear();
     if (n_iters < 0) return fail(h, BP_ERR_ARG, "bp_iterate: n_iters < 0");
@@ -771,6 +781,7 @@ bp_status bp_iterate(bp_handle h, int n_iters, int mode, bp_schedule schedule) {
 }
 
 bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind) {
+    BPG_TRACE("bp_iterate_dense");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_iterate_dense: NULL handle");
     h->err.clear();
     if (n_iters < 0) return fail(h, BP_ERR_ARG, "bp_iterate_dense: n_iters < 0");
@@ -817,6 +828,7 @@ bp_status bp_iterate_dense(bp_handle h, int n_iters, bp_dense_kind kind) {
 }
 
 bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map) {
+    BPG_TRACE("bp_beliefs");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_beliefs: NULL handle");
     h->err.clear();
     if (!dev_out) return fail(h, BP_ERR_ARG, "bp_beliefs: NULL output");
@@ -839,6 +851,7 @@ bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map) {
 }
 
 bp_status bp_get_messages(bp_handle h, void *dev_planes) {
+    BPG_TRACE("bp_get_messages");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_get_messages: NULL handle");
     h->err.clear();
     if (!dev_planes) return fail(h, BP_ERR_ARG, "bp_get_messages: NULL output");
@@ -856,6 +869,7 @@ bp_status bp_get_messages(bp_handle h, void *dev_planes) {
 }
 
 bp_status bp_set_messages(bp_handle h, const void *dev_planes) {
+    BPG_TRACE("bp_set_messages");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_set_messages: NULL handle");
     h->err.clear();
     if (!dev_planes) return fail(h, BP_ERR_ARG, "bp_set_messages: NULL input");
@@ -874,6 +888,7 @@ bp_status bp_set_messages(bp_handle h, const void *dev_planes) {
 }
 
 bp_status bp_sync(bp_handle h) {
+    BPG_TRACE("bp_sync");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_sync: NULL handle");
     BP_CK(h, cudaStreamSynchronize(h->stream));
     int flag = 0;
@@ -886,6 +901,7 @@ bp_status bp_sync(bp_handle h) {
 }
 
 bp_status bp_autotune(bp_handle h, int mode, int n_iters, float *host_best_ms) {
+    BPG_TRACE("bp_autotune");
     if (!h) return fail(nullptr, BP_ERR_ARG, "bp_autotune: NULL handle");
     h->err.clear();
     if (n_iters < 1) return fail(h, BP_ERR_ARG, "bp_autotune: n_iters < 1");
@@ -949,6 +965,7 @@ bp_status bp_set_grid(bp_handle h, int blocks) {
 
 bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int *KM, int *LM,
                              int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent) {
+    BPG_TRACE("bp_sparse_schedule");
     g_global_err.clear();
     if (M < 2 || M > 1024) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: M out of range");
     if (!host_rowptr || !KM || !LM || !steps || !wavefronts || (!host_cols && host_rowptr[M] != 0))

@@ -12,6 +12,7 @@
 
 #include <vector>
 
+#include "trace.h"
 #include "bp_adjoint.h"
 #include "bp_ctx.h"
 
@@ -117,6 +118,7 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
 
 extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
                                  double *host_dfbar) {
+    BPG_TRACE("bp_backward");
     if (!h) return bpg_fail(nullptr, BP_ERR_ARG, "bp_backward: NULL handle");
     h->err.clear();
     if (!dev_dlogb || !dev_dlogg || !host_dtable || !host_dfbar)

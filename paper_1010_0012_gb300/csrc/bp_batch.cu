@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "trace.h"
 #include "../../include/bp.h"
 #include "bp_batch_internal.h"
 #include "bp_ctx.h"
@@ -86,6 +87,7 @@ struct bp_batch_ctx {
 
 static bp_status bfail(bp_batch b, bp_status st, const std::string &m) {
     if (b) b->err = m; else g_batch_err = m;
+    if (st != BP_OK) log_error(st, m);
     return st;
 }
 
@@ -225,6 +227,7 @@ void bp_batch_destroy(bp_batch b) {
 }
 
 bp_status bp_batch_create(int n, const bp_mrf_desc *descs, bp_dtype dtype, void *cuda_stream, bp_batch *out) {
+    BPG_TRACE("bp_batch_create");
     g_batch_err.clear();
     if (!out) return bfail(nullptr, BP_ERR_ARG, "bp_batch_create: out is NULL");
     *out = nullptr;
@@ -363,6 +366,7 @@ static bool tiling_ok(int family, int tile_words) {
 }
 
 bp_status bp_batch_set_tiling(bp_batch b, int family, int tile_words) {
+    BPG_TRACE("bp_batch_set_tiling");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_set_tiling: NULL batch");
     b->err.clear();
     if (!tiling_ok(family, tile_words))
@@ -402,6 +406,7 @@ bp_status bp_batch_get_class_tiling(bp_batch b, int k, int *Mp, int *T, int *fam
 }
 
 bp_status bp_batch_set_class_tiling(bp_batch b, int Mp, int T, int family, int tile_words) {
+    BPG_TRACE("bp_batch_set_class_tiling");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_set_class_tiling: NULL batch");
     b->err.clear();
     auto it = b->class_cfg.find({Mp, T});
@@ -425,6 +430,7 @@ bp_status bp_batch_set_wait_limit(bp_batch b, double seconds, int extra_arrivals
 }
 
 bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode) {
+    BPG_TRACE("bp_batch_iterate");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_iterate: NULL batch");
     b->err.clear();
     if (n_iters < 0) return bfail(b, BP_ERR_ARG, "bp_batch_iterate: n_iters < 0");
@@ -472,6 +478,7 @@ bp_status bp_batch_iterate(bp_batch b, int n_iters, int mode) {
 }
 
 bp_status bp_batch_sync(bp_batch b) {
+    BPG_TRACE("bp_batch_sync");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_sync: NULL batch");
     BB_CK(b, cudaStreamSynchronize(b->stream));
     int flag = 0;
@@ -485,6 +492,7 @@ bp_status bp_batch_sync(bp_batch b) {
 }
 
 bp_status bp_batch_beliefs(bp_batch b, int k, void *dev_out, int32_t *dev_map) {
+    BPG_TRACE("bp_batch_beliefs");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_beliefs: NULL batch");
     b->err.clear();
     if (k < 0 || k >= b->n || !dev_out) return bfail(b, BP_ERR_ARG, "bp_batch_beliefs: bad index or NULL output");
@@ -502,6 +510,7 @@ bp_status bp_batch_beliefs(bp_batch b, int k, void *dev_out, int32_t *dev_map) {
 }
 
 bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes) {
+    BPG_TRACE("bp_batch_get_messages");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_get_messages: NULL batch");
     b->err.clear();
     if (k < 0 || k >= b->n || !dev_planes) return bfail(b, BP_ERR_ARG, "bp_batch_get_messages: bad index or NULL output");
@@ -521,6 +530,7 @@ bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes) {
 // keyed by the batch's classes and size (path: $BP_AUTOTUNE_CACHE, if set).
 // Leaves the messages reset to the uniform state.
 bp_status bp_batch_autotune(bp_batch b, int mode, int n_iters, float *host_best_ms) {
+    BPG_TRACE("bp_batch_autotune");
     if (!b) return bfail(nullptr, BP_ERR_ARG, "bp_batch_autotune: NULL batch");
     b->err.clear();
     if (n_iters < 1) return bfail(b, BP_ERR_ARG, "bp_batch_autotune: n_iters < 1");

@@ -15,6 +15,7 @@
 
 #include <vector>
 
+#include "trace.h"
 #include "bp_ctx.h"
 
 namespace {
@@ -105,6 +106,7 @@ void bpg_free_levels(bp_ctx *h) {
 
 extern "C" bp_status bp_iterate_multiscale(bp_handle h, int n_levels, const int *host_iters, int mode,
                                            bp_schedule schedule) {
+    BPG_TRACE("bp_iterate_multiscale");
     if (!h) return bpg_fail(nullptr, BP_ERR_ARG, "bp_iterate_multiscale: NULL handle");
     h->err.clear();
     if (n_levels < 1 || n_levels > 16 || !host_iters) return bpg_fail(h, BP_ERR_ARG, "bp_iterate_multiscale: bad levels");

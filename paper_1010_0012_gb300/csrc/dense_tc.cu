@@ -31,6 +31,7 @@
 #include <string>
 #include <vector>
 
+#include "trace.h"
 #include "bp_ctx.h"
 #include "dense_tc_ring.h"
 #include "tc_ptx.cuh"
@@ -747,6 +748,7 @@ static __device__ __align__(256) uint8_t bpg_noalloc_scratch[kNoAllocBytes];
 extern "C" bp_status bp_iterate_dense_tc_noalloc(int W, int H, int M, const float *dev_unary,
                                                  const float *dev_in_planes, float *dev_out_planes,
                                                  const float *host_table, int T, double fbar, void *cuda_stream) {
+    BPG_TRACE("bp_iterate_dense_tc_noalloc");
     bpg_fail(nullptr, BP_OK, "");
     if (W < 1 || H < 1) return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: W and H must be >= 1");
     if (M != 64 && M != 128) return noalloc_fail(BP_ERR_ARG, "bp_iterate_dense_tc_noalloc: M must be 64 or 128");

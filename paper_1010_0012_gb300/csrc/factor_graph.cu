@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "trace.h"
 #include "../../include/bp.h"
 #include "bp_internal.h"
 
@@ -371,6 +372,7 @@ struct bp_fg_ctx {
 
 static bp_status fgfail(bp_factor_graph g, bp_status st, const std::string &m) {
     if (g) g->err = m; else g_fg_err = m;
+    if (st != BP_OK) bpg::log_error(st, m);
     return st;
 }
 
@@ -427,6 +429,7 @@ void bp_fg_destroy(bp_factor_graph g) {
 
 bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_factor_vars, bp_dtype dtype,
                        void *cuda_stream, bp_factor_graph *out) {
+    BPG_TRACE("bp_fg_create");
     g_fg_err.clear();
     if (!out) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_create: out is NULL");
     *out = nullptr;
@@ -476,6 +479,7 @@ bp_status bp_fg_create(int n_vars, int M, int n_factors, const int32_t *host_fac
 }
 
 bp_status bp_fg_set_unary(bp_factor_graph g, const void *dev_unary) {
+    BPG_TRACE("bp_fg_set_unary");
     if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_set_unary: NULL graph");
     g->err.clear();
     if (!dev_unary) return fgfail(g, BP_ERR_ARG, "bp_fg_set_unary: NULL unary");
@@ -493,6 +497,7 @@ bp_status bp_fg_set_unary(bp_factor_graph g, const void *dev_unary) {
 
 bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplets, const void *host_vals,
                            double fbar) {
+    BPG_TRACE("bp_fg_set_factor");
     if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_set_factor: NULL graph");
     g->err.clear();
     if (C < 0 || (C > 0 && (!host_triplets || !host_vals)))
@@ -654,6 +659,7 @@ static bp_status fg_v2f(bp_factor_graph g) {
 }
 
 bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode) {
+    BPG_TRACE("bp_fg_iterate");
     if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_iterate: NULL graph");
     g->err.clear();
     if (n_iters < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_iterate: n_iters < 0");
@@ -677,6 +683,7 @@ bp_status bp_fg_iterate(bp_factor_graph g, int n_iters, int mode) {
 }
 
 bp_status bp_fg_iterate_dense(bp_factor_graph g, int n_iters, int mode) {
+    BPG_TRACE("bp_fg_iterate_dense");
     if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_iterate_dense: NULL graph");
     g->err.clear();
     if (n_iters < 0) return fgfail(g, BP_ERR_ARG, "bp_fg_iterate_dense: n_iters < 0");
@@ -711,6 +718,7 @@ bp_status bp_fg_iterate_dense(bp_factor_graph g, int n_iters, int mode) {
 }
 
 bp_status bp_fg_beliefs(bp_factor_graph g, void *dev_out, int32_t *dev_map) {
+    BPG_TRACE("bp_fg_beliefs");
     if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_beliefs: NULL graph");
     g->err.clear();
     if (!dev_out) return fgfail(g, BP_ERR_ARG, "bp_fg_beliefs: NULL output");
@@ -739,6 +747,7 @@ bp_status bp_fg_get_messages(bp_factor_graph g, void *dev_out) {
 }
 
 bp_status bp_fg_sync(bp_factor_graph g) {
+    BPG_TRACE("bp_fg_sync");
     if (!g) return fgfail(nullptr, BP_ERR_ARG, "bp_fg_sync: NULL graph");
     FG_CK(g, cudaStreamSynchronize(g->stream));
     return BP_OK;
