@@ -180,8 +180,9 @@ bp_status bp_beliefs(bp_handle h, void *dev_out, int32_t *dev_map);
 /* Copy the current message planes out / in: the messages m_ij(x_j) of Eq. 2
  * ([4][H][W][M], dtype of the handle).  Float32 messages cross this boundary linear (normalised) in every
  * mode: after log-mode iterations bp_get_messages returns exp of the
- * log-domain state, and bp_set_messages installs a linear state.  Used to
- * checkpoint or inject a state. */
+ * log-domain state, and bp_set_messages installs a linear state.  Slots
+ * without a neighbour (never read by any update) come out as 0 and are
+ * ignored on the way in.  Used to checkpoint or inject a state. */
 bp_status bp_get_messages(bp_handle h, void *dev_planes);
 bp_status bp_set_messages(bp_handle h, const void *dev_planes);
 

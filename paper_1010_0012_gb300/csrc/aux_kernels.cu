@@ -471,6 +471,26 @@ __global__ void log_copy_kernel(const float *g, float *lg, long long nodes, int 
         lg[i] = x < M ? log2f(g[i]) : 0.f;
     }
 }
+// Message planes [4][H][W][Mp] -> [4][H][W][M]; slots without a neighbour
+// (never read by any update) come out as 0, the log domain (base 2) as linear.
+__global__ void unpad_messages_kernel(const int32_t *src, int32_t *dst, int W, int H, int M, int Mp, int exp2_log) {
+    const long long n = 4LL * W * H * M;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long row = i / M;
+        const int x = (int)(i - row * M);
+        const int pl = (int)(row / ((long long)W * H));
+        const long long node = row - (long long)pl * W * H;
+        const int r = (int)(node / W), c = (int)(node - (long long)r * W);
+        const bool has = pl == 0 ? c > 0 : pl == 1 ? c < W - 1 : pl == 2 ? r > 0 : r < H - 1;
+        int32_t v = 0;
+        if (has) {
+            v = src[row * Mp + x];
+            if (exp2_log) v = __float_as_int(exp2f(__int_as_float(v)));
+        }
+        dst[i] = v;
+    }
+}
+
 __global__ void convert_dense_kernel(float *p, long long n, int to_log) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         p[i] = to_log ? log2f(p[i]) : exp2f(p[i]);
@@ -483,6 +503,12 @@ cudaError_t launch_domain_convert(float *planes, long long rows, int M, int Mp, 
 }
 cudaError_t launch_domain_convert_copy(const float *g, float *logg, long long nodes, int M, int Mp, cudaStream_t s) {
     log_copy_kernel<<<grid_for(nodes * Mp, 256), 256, 0, s>>>(g, logg, nodes, M, Mp);
+    return cudaGetLastError();
+}
+cudaError_t launch_unpad_messages(const void *src, void *dst, int W, int H, int M, int Mp, int exp2_log,
+                                  cudaStream_t s) {
+    unpad_messages_kernel<<<grid_for(4LL * W * H * M, 256), 256, 0, s>>>((const int32_t *)src, (int32_t *)dst, W, H,
+                                                                         M, Mp, exp2_log);
     return cudaGetLastError();
 }
 cudaError_t launch_domain_convert_dense(float *p, long long n, int to_log, cudaStream_t s) {

@@ -858,13 +858,9 @@ bp_status bp_get_messages(bp_handle h, void *dev_planes) {
     if (bp_status st = bpg_check_device(h)) return st;
     if (h->msg_uniform)
         if (bp_status st = materialize(h, false)) return st;
-    const long long rows = 4LL * h->W * h->H;
-    BP_CK(h, launch_unpad_copy(h->msg[h->cur], dev_planes, rows, h->M, h->Mp, h->stream));
+    BP_CK(h, launch_unpad_messages(h->msg[h->cur], dev_planes, h->W, h->H, h->M, h->Mp,
+                                   h->dtype == BP_F32 && h->msg_log ? 1 : 0, h->stream));
     h->launches += 1;
-    if (h->dtype == BP_F32 && h->msg_log) {
-        BP_CK(h, launch_domain_convert_dense((float *)dev_planes, rows * h->M, 0, h->stream));
-        h->launches += 1;
-    }
     return BP_OK;
 }
 

@@ -516,7 +516,7 @@ bp_status bp_batch_get_messages(bp_batch b, int k, void *dev_planes) {
     if (k < 0 || k >= b->n || !dev_planes) return bfail(b, BP_ERR_ARG, "bp_batch_get_messages: bad index or NULL output");
     if (bp_status st = materialize_batch(b)) return st;
     const MrfHost &m = b->mrfs[k];
-    BB_CK(b, launch_unpad_copy(m.msg[b->cur], dev_planes, 4LL * m.W * m.H, m.M, m.Mp, b->stream));
+    BB_CK(b, launch_unpad_messages(m.msg[b->cur], dev_planes, m.W, m.H, m.M, m.Mp, 0, b->stream));
     b->launches += 1;
     return BP_OK;
 }

@@ -128,6 +128,9 @@ cudaError_t launch_pad_copy_i32(const int32_t *src, int32_t *dst, long long node
                                 cudaStream_t s);
 cudaError_t launch_unpad_copy(const void *src, void *dst, long long rows, int M, int Mp,
                               cudaStream_t s);   // 4-byte elements
+// message planes out: slots without a neighbour as 0; exp2_log: base-2 log state to linear
+cudaError_t launch_unpad_messages(const void *src, void *dst, int W, int H, int M, int Mp, int exp2_log,
+                                  cudaStream_t s);
 cudaError_t launch_fill_messages_f32(float *planes, long long nodes4, int M, int Mp, float value,
                                      cudaStream_t s);
 cudaError_t launch_fill_messages_i32(int32_t *planes, long long nodes4, int M, int Mp,
