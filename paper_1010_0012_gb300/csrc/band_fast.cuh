@@ -313,8 +313,17 @@ struct SumBand {
     }
 };
 
+template <bool LOG>
+struct SumArgsOf {
+    using type = BandArgsF;
+};
+template <>
+struct SumArgsOf<true> {
+    using type = BandArgsLogF;
+};
+
 template <int L, int C, int T, bool LOG, bool FULL = false>
-__global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
+__global__ void __launch_bounds__(kBlock) band_sum_kernel(const typename SumArgsOf<LOG>::type a) {
     constexpr int GPB = kBlock / L;
     const int grp = threadIdx.x / L;
     SumBand<L, C, T, LOG, false, FULL> band;
@@ -324,7 +333,10 @@ __global__ void __launch_bounds__(kBlock) band_sum_kernel(const BandArgsF a) {
     for (int base = blockIdx.x * GPB; base < nslots; base += gridDim.x * GPB) {
         int r, c;
         const bool valid = slot_node(base + grp, nslots, W, a.parity, r, c);
-        band.node(a.g, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid, LOG ? a.stats : nullptr);
+        if constexpr (LOG)
+            band.node(a.g, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid, a.stats);
+        else
+            band.node(a.g, a.in, a.out, W, a.d.H, a.d.Mp, a.d.plane, r, c, valid);
     }
 }
 

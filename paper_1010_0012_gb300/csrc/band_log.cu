@@ -16,7 +16,7 @@ struct LogFullTag {
     static const void *get() { return (const void *)band_sum_kernel<L, C, T, true, true>; }
 };
 
-cudaError_t launch_band_log(const BandArgsF &a, Layout lay, int blocks, cudaStream_t s) {
+cudaError_t launch_band_log(const BandArgsLogF &a, Layout lay, int blocks, cudaStream_t s) {
     return a.d.M == a.d.Mp ? launch_fast<LogFullTag>(a, lay, blocks, s) : launch_fast<LogTag>(a, lay, blocks, s);
 }
 

@@ -167,7 +167,7 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
                 e = launch_band_min_generic(a, h->stream);
             }
         } else if (h->fast) {
-            BandArgsF a{};
+            BandArgsLogF a{};   // stats stay NULL: only the recorded run keeps the scales
             a.g = is_log ? h->log_unary : (const float *)h->unary;
             a.in = (const float *)in; a.out = (float *)out;
             a.d = h->dims; a.parity = parity; a.T = h->Teff;

@@ -36,8 +36,8 @@ void bpg_free_extras(bp_ctx *h) {
         if (e_ != cudaSuccess) return bpg_cuda_fail((h), e_, #call);     \
     } while (0)
 
-static BandArgsF log_args(bp_ctx *h, const void *in, void *out) {
-    BandArgsF a{};
+static BandArgsLogF log_args(bp_ctx *h, const void *in, void *out) {
+    BandArgsLogF a{};
     a.g = h->log_unary;
     a.in = (const float *)in;
     a.out = (float *)out;
@@ -102,7 +102,7 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
             out = (char *)h->seg_buf + (size_t)(t1 - last_start - 1) * sb;
         else
             out = state == h->msg[0] ? h->msg[1] : h->msg[0];
-        BandArgsF la = log_args(h, state, out);
+        BandArgsLogF la = log_args(h, state, out);
         la.stats = (float2 *)h->stats_buf + (size_t)t * stats_per_iter;
         BK_CK(h, launch_band_log(la, h->rec_layout, h->blocks_override, h->stream));
         h->launches += 1;

@@ -31,9 +31,14 @@ struct BandArgsF {
     int T;
     float w[2 * kTMaxFast + 1];  // f(d) - fbar, d = -T..T
     float fbar;
-    // log mode only, nullable: per message [H][W][4] the forward's scale
-    // C = A + log2 Z (A the max shift, Z the normaliser) and S / Z, read by
-    // the adjoint kernel instead of recomputing them
+};
+
+// The log-domain kernel's arguments: those of the linear one and, nullable,
+// the per-message output [H][W][4] of the forward's scale C = A + log2 Z
+// (A the max shift, Z the normaliser) and S / Z, which the adjoint reads
+// instead of recomputing them.  (A type of its own, so that the linear
+// kernel's parameters stay as they are.)
+struct BandArgsLogF : BandArgsF {
     float2 *stats;
 };
 
@@ -103,7 +108,7 @@ int padded_labels(int M);   // Mp for a label count M
 // persistent grid (SM count x resident blocks per SM).
 cudaError_t launch_band_sum(const BandArgsF &a, Layout lay, int blocks, cudaStream_t s);
 cudaError_t launch_band_min(const BandArgsI &a, Layout lay, int blocks, cudaStream_t s);
-cudaError_t launch_band_log(const BandArgsF &a, Layout lay, int blocks, cudaStream_t s);
+cudaError_t launch_band_log(const BandArgsLogF &a, Layout lay, int blocks, cudaStream_t s);
 bool band_fast_available(int Mp, Layout lay, int T);
 
 cudaError_t launch_band_sum_generic(const BandArgsGenericF &a, cudaStream_t s);
