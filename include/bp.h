@@ -367,7 +367,12 @@ bp_status bp_set_persistent(bp_handle h, int mode);
  *                        its entries scheduled on the host so that the
  *                        shared-memory gathers do not conflict (M <= 256 and
  *                        a schedule of at most 48, 24, 12 or 6 steps per
- *                        32-label block for M <= 32, 64, 128, 256);
+ *                        32-label block for M <= 32, 64, 128, 256).
+ *                        Min-sum with Ebar <= 16382 runs it on 16-bit label
+ *                        pairs: h - min h clamped to Ebar + 1 (terms above
+ *                        never beat the flat term Ebar + min h), two
+ *                        directions per add-min; the messages equal the
+ *                        32-bit kernel's exactly;
  *   BP_SPARSE_AUTO       (default) the register kernel where the pattern has
  *                        a schedule, else the lists.
  * bp_set_sparse_kernel returns BP_ERR_UNSUPPORTED when the current pattern has
@@ -381,17 +386,21 @@ bp_status bp_get_sparse_kernel(bp_handle h, int *kind, int *steps, int *wavefron
 
 /* The register kernel's schedule of a pattern, computed on the host only (no
  * device, no handle; no counterpart in the paper).  Pattern as for
- * bp_set_potential_sparse (CSR by receiver label, M labels).  *KM = 32-label
- * receiver blocks, *LM = register steps per block, *steps = the longest
- * quarter-warp schedule, *wavefronts = gather wavefronts per node; all 0 when
- * the pattern has no register schedule.  host_lab [KM][32] (nullable)
- * receives each lane's receiver label (-1: none); host_ent [KM][LM][32][2]
- * (nullable) each lane's entry per step: the byte offset of the sender label's
- * h slot (0xFFFF for a hole) and the entry's CSR position in host_cols.
- * Call with NULL buffers first to learn KM and LM.  Errors through
- * bp_last_error(NULL). */
-bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int *KM, int *LM,
-                             int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent);
+ * bp_set_potential_sparse (CSR by receiver label, M labels).  gather_bytes:
+ * 16 for the FP32 / int32 kernels (16-byte h slots, label x in slot
+ * (x & ~31) | ((x & 3) << 3) | ((x >> 2) & 7), served to quarter-warps from
+ * eight 16-byte bank groups), 8 for the 16-bit min-sum form that min-sum
+ * potentials with Ebar <= 16382 run (8-byte slots
+ * (x & ~63) | ((x & 3) << 4) | ((x >> 2) & 15), half-warps, sixteen 8-byte
+ * groups).  *KM = 32-label receiver blocks, *LM = register steps per block,
+ * *steps = LM, *wavefronts = gather wavefronts per node; all 0 when the
+ * pattern has no register schedule.  host_lab [KM][32] (nullable) receives
+ * each lane's receiver label (-1: none); host_ent [KM][LM][32][2] (nullable)
+ * each lane's entry per step: the byte offset of the sender label's h slot
+ * (0xFFFF for a hole) and the entry's CSR position in host_cols.  Call with
+ * NULL buffers first to learn KM and LM.  Errors through bp_last_error(NULL). */
+bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int gather_bytes,
+                             int *KM, int *LM, int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent);
 
 /* ---- factor graphs with three-variable factors (Sec. 7) --------------------
  * Variables v = 0..n_vars-1 with M labels and unaries g_v (or energies E_v);

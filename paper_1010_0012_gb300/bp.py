@@ -58,7 +58,7 @@ def _load():
         "bp_set_persistent": ([P, I], I),
         "bp_set_sparse_kernel": ([P, I], I),
         "bp_get_sparse_kernel": ([P, P, P, P], I),
-        "bp_sparse_schedule": ([I, P, P, P, P, P, P, P, P], I),
+        "bp_sparse_schedule": ([I, P, P, I, P, P, P, P, P, P], I),
         "bp_set_grid": ([P, I], I),
         "bp_sync": ([P], I),
         "bp_last_error": ([P], ctypes.c_char_p),
@@ -260,23 +260,24 @@ def bp_set_sparse_kernel(h, kind):
     _check(h, _lib.bp_set_sparse_kernel(h, int(kind)))
 
 
-def bp_sparse_schedule(M, rowptr, cols):
-    """The register kernel's schedule of a CSR pattern (host only): dict with
-    KM, LM, steps, wavefronts, lab [KM][32] and ent [KM][LM][32][2] (byte
-    offset of the h slot or 0xFFFF, CSR position), or None without one."""
+def bp_sparse_schedule(M, rowptr, cols, gather_bytes=16):
+    """The register kernel's schedule of a CSR pattern (host only) for 16-byte
+    (FP32 / int32) or 8-byte (16-bit min-sum) gathers: dict with KM, LM,
+    steps, wavefronts, lab [KM][32] and ent [KM][LM][32][2] (byte offset of
+    the h slot or 0xFFFF, CSR position), or None without one."""
     import numpy as np
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     cl = np.ascontiguousarray(cols, dtype=np.int32)
     v = [ctypes.c_int() for _ in range(4)]
     vp = rp.ctypes.data_as(ctypes.c_void_p)
     cp = cl.ctypes.data_as(ctypes.c_void_p) if cl.size else None
-    _check(None, _lib.bp_sparse_schedule(int(M), vp, cp, *[ctypes.byref(x) for x in v], None, None))
+    _check(None, _lib.bp_sparse_schedule(int(M), vp, cp, int(gather_bytes), *[ctypes.byref(x) for x in v], None, None))
     KM, LM, steps, wf = (x.value for x in v)
     if KM == 0:
         return None
     lab = np.empty((KM, 32), np.int32)
     ent = np.empty((KM, LM, 32, 2), np.int32)
-    _check(None, _lib.bp_sparse_schedule(int(M), vp, cp, *[ctypes.byref(x) for x in v],
+    _check(None, _lib.bp_sparse_schedule(int(M), vp, cp, int(gather_bytes), *[ctypes.byref(x) for x in v],
                                          lab.ctypes.data_as(ctypes.c_void_p), ent.ctypes.data_as(ctypes.c_void_p)))
     return {"KM": KM, "LM": LM, "steps": steps, "wavefronts": wf, "lab": lab, "ent": ent}
 

@@ -131,9 +131,10 @@ static cudaError_t issue_iteration(bp_ctx *h, int mode, int sched, int &cur, int
             if (is_log) return cudaErrorNotSupported;
             if (h->sp_reg && h->sp_kernel != BP_SPARSE_LISTS) {
                 SparseRegArgs a{h->unary, in, out, h->dims, parity, (const int2 *)h->d_sp_rent,
-                                (const int32_t *)h->d_sp_rlab, h->fbarf, h->ebar, h->d_status};
-                e = h->dtype == BP_I32 ? launch_sparse_reg_min(a, h->sp_KM, h->sp_LM, h->stream)
-                                       : launch_sparse_reg_sum(a, h->sp_KM, h->sp_LM, h->stream);
+                                (const int32_t *)h->d_sp_rlab, h->fbarf, h->ebar, h->d_status, {}};
+                e = h->dtype != BP_I32 ? launch_sparse_reg_sum(a, h->sp_KM, h->sp_LM, h->stream)
+                    : h->sp_p16        ? launch_sparse_reg_min16(a, h->sp_KM, h->sp_LM, h->stream)
+                                       : launch_sparse_reg_min(a, h->sp_KM, h->sp_LM, h->stream);
                 if (e != cudaSuccess) return e;
                 ++count;
                 continue;
@@ -678,21 +679,27 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
             ell[((size_t)i * h->M + xj) * 2] = sp_label_slot(host_cols[p]);
             ell[((size_t)i * h->M + xj) * 2 + 1] = wbits[p];
         }
-    // the register-pattern schedule, when the pattern fits one (else the list kernels serve)
+    // the register-pattern schedule, when the pattern fits one (else the list
+    // kernels serve); min-sum with Ebar <= kP16MaxEbar runs on 16-bit label pairs
+    const bool p16 = h->dtype == BP_I32 && (int32_t)fbar <= kP16MaxEbar;
     SparseRegPlan plan;
-    const bool reg_ok = sparse_reg_plan(h->M, h->Mp, host_rowptr, host_cols, wbits.data(), &plan);
+    const bool reg_ok = sparse_reg_plan(h->M, h->Mp, host_rowptr, host_cols, wbits.data(), p16 ? 8 : 16, &plan);
     BP_CK(h, cudaStreamSynchronize(h->stream));   // earlier work may still read the old pattern
     void *bufs[] = {h->d_sp_len, h->d_sp_ell, h->d_sp_rent, h->d_sp_rlab};
     for (void *p : bufs)
         if (p) cudaFree(p);
     h->d_sp_len = h->d_sp_ell = h->d_sp_rent = h->d_sp_rlab = nullptr;
     h->sp_reg = false;
+    h->sp_p16 = false;
     if (bp_status st = ensure_buffer(h, &h->d_sp_len, (size_t)h->M * 4, "sparse row lengths")) return st;
     if (bp_status st = ensure_buffer(h, &h->d_sp_ell, ell.size() * 4, "sparse pattern")) return st;
     BP_CK(h, cudaMemcpyAsync(h->d_sp_len, len.data(), (size_t)h->M * 4, cudaMemcpyHostToDevice, h->stream));
     BP_CK(h, cudaMemcpyAsync(h->d_sp_ell, ell.data(), ell.size() * 4, cudaMemcpyHostToDevice, h->stream));
     if (reg_ok) {
-        const std::vector<int32_t> dent = sparse_reg_device_entries(plan, h->dtype == BP_I32);
+        const SparseRegMode rmode = h->dtype != BP_I32 ? SparseRegMode::Sum
+                                    : p16                ? SparseRegMode::Min16
+                                                         : SparseRegMode::Min;
+        const std::vector<int32_t> dent = sparse_reg_device_entries(plan, rmode, h->ebar);
         if (bp_status st = ensure_buffer(h, &h->d_sp_rent, dent.size() * 4, "register pattern")) return st;
         if (bp_status st = ensure_buffer(h, &h->d_sp_rlab, plan.lab.size() * 4, "register pattern labels"))
             return st;
@@ -700,6 +707,7 @@ bp_status bp_set_potential_sparse(bp_handle h, const int32_t *host_rowptr, const
         BP_CK(h, cudaMemcpyAsync(h->d_sp_rlab, plan.lab.data(), plan.lab.size() * 4, cudaMemcpyHostToDevice,
                                  h->stream));
         h->sp_reg = true;
+        h->sp_p16 = p16;
         h->sp_KM = plan.KM;
         h->sp_LM = plan.LM;
         h->sp_steps = plan.steps;
@@ -959,13 +967,15 @@ bp_status bp_set_grid(bp_handle h, int blocks) {
     return BP_OK;
 }
 
-bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int *KM, int *LM,
-                             int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent) {
+bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *host_cols, int gather_bytes,
+                             int *KM, int *LM, int *steps, int *wavefronts, int32_t *host_lab, int32_t *host_ent) {
     BPG_TRACE("bp_sparse_schedule");
     g_global_err.clear();
     if (M < 2 || M > 1024) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: M out of range");
     if (!host_rowptr || !KM || !LM || !steps || !wavefronts || (!host_cols && host_rowptr[M] != 0))
         return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: NULL argument");
+    if (gather_bytes != 16 && gather_bytes != 8)
+        return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: gather_bytes must be 16 or 8");
     if (host_rowptr[0] != 0) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: rowptr[0] must be 0");
     for (int x = 0; x < M; ++x)
         if (host_rowptr[x + 1] < host_rowptr[x]) return fail(nullptr, BP_ERR_ARG, "bp_sparse_schedule: rowptr decreases");
@@ -976,7 +986,8 @@ bp_status bp_sparse_schedule(int M, const int32_t *host_rowptr, const int32_t *h
     for (int p = 0; p < host_rowptr[M]; ++p) index[p] = p;
     SparseRegPlan plan;
     *KM = *LM = *steps = *wavefronts = 0;
-    if (!sparse_reg_plan(M, padded_labels(M), host_rowptr, host_cols, index.data(), &plan)) return BP_OK;
+    if (!sparse_reg_plan(M, padded_labels(M), host_rowptr, host_cols, index.data(), gather_bytes, &plan))
+        return BP_OK;
     *KM = plan.KM;
     *LM = plan.LM;
     *steps = plan.steps;

@@ -61,6 +61,7 @@ struct bp_ctx {
     void *d_sp_len = nullptr, *d_sp_ell = nullptr;   // device pattern (see bp_sparse.h)
     // register-pattern schedule (sparse_reg_plan.cu), when the pattern fits one
     bool sp_reg = false;
+    bool sp_p16 = false;    // min-sum register kernel on 16-bit label pairs (Ebar <= kP16MaxEbar)
     int sp_KM = 0, sp_LM = 0, sp_steps = 0, sp_wavefronts = 0;
     void *d_sp_rent = nullptr, *d_sp_rlab = nullptr;
     int sp_kernel = 0;               // BP_SPARSE_AUTO / _LISTS / _REGISTERS

@@ -52,6 +52,14 @@ cudaError_t launch_sparse_min(const SparseArgsI &a, cudaStream_t s);
 // always a label) with the value 0.0f (sum: adds nothing) or kSparseHoleE
 // (min-sum: E + h never goes below Ebar + min h, the flat term).
 constexpr int32_t kSparseHoleE = 1 << 29;
+// Largest Ebar of the 16-bit min-sum form: its operands stay in [0, 2 Ebar + 2].
+constexpr int32_t kP16MaxEbar = 16382;
+
+// How a launch walks its nodes: slots per row, and the grid stride in whole
+// rows and remaining slots (set by the launcher).
+struct SparseWalk {
+    int row, dq, dr;
+};
 
 struct SparseRegArgs {
     const void *u;           // [H][W][Mp] g (float) or E_u (int32)
@@ -64,6 +72,7 @@ struct SparseRegArgs {
     float fbar;
     int32_t ebar;
     int *status;             // device error word: 301 when a bounded wait gave up
+    SparseWalk walk;         // set by the launcher
 };
 
 // (KM, LM) pairs compiled: KM = 32-label receiver blocks (Mp <= 32 KM), LM =
@@ -73,25 +82,31 @@ constexpr int kSparseRegVariants[][2] = {{1, 16}, {1, 48}, {2, 8}, {2, 12}, {2, 
 
 struct SparseRegPlan {
     int KM = 0, LM = 0;
+    int gather_bytes = 16;         // 16: FP32 / int32 slots; 8: the 16-bit min-sum form
     int steps = 0;                 // steps every lane runs per block (= LM)
-    int wavefronts = 0;            // gather wavefronts per node (sum over blocks, quarter-warps, steps)
+    int wavefronts = 0;            // gather wavefronts per node (sum over blocks, lane sets, steps)
     std::vector<int32_t> ent;      // [KM][LM][32][2]
     std::vector<int32_t> lab;      // [KM][32]
 };
 
 // Schedules a pattern (CSR by receiver label; wbits = value bits per entry)
-// for the register kernels; holes have offset 0xFFFF.  False when Mp > 256
-// or when a list is longer than the steps of every compiled variant (the list
-// kernels serve it).
+// for the register kernels with gathers of gather_bytes (16: quarter-warps,
+// 8: half-warps); holes have offset 0xFFFF.  False when Mp > 256 or when a
+// list is longer than the steps of every compiled variant (the list kernels
+// serve it).
 bool sparse_reg_plan(int M, int Mp, const int32_t *rowptr, const int32_t *cols, const int32_t *wbits,
-                     SparseRegPlan *out);
+                     int gather_bytes, SparseRegPlan *out);
+
+enum class SparseRegMode { Sum, Min, Min16 };
 
 // The entries as the kernel takes them: a hole reads a slot that another lane
-// of its quarter-warp reads at that step (no extra wavefront), or slot 0, with
-// a value that changes nothing.
-std::vector<int32_t> sparse_reg_device_entries(const SparseRegPlan &plan, bool min_sum);
+// of its lane set reads at that step (no extra wavefront), or slot 0, with a
+// value that changes nothing (0.0f; kSparseHoleE; Ebar + 1 in both halves of
+// the 16-bit form, whose weights are E in both halves).
+std::vector<int32_t> sparse_reg_device_entries(const SparseRegPlan &plan, SparseRegMode mode, int32_t ebar);
 
 cudaError_t launch_sparse_reg_sum(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);
 cudaError_t launch_sparse_reg_min(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);
+cudaError_t launch_sparse_reg_min16(const SparseRegArgs &a, int KM, int LM, cudaStream_t s);
 
 }  // namespace bpg

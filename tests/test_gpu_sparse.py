@@ -77,14 +77,24 @@ def test_sparse_sum_matches_oracle(M, k, schedule, kernel):
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("M,k", [(16, 5), (64, 7), (200, 6)])
 @pytest.mark.parametrize("schedule", ["sync", "redblack"])
-def test_sparse_min_matches_oracle_bit_exact(M, k, schedule, kernel):
+@pytest.mark.parametrize("ebar", [40, 16382, 16383])
+def test_sparse_min_matches_oracle_bit_exact(M, k, schedule, kernel, ebar):
+    """Ebar <= 16382 runs the register kernel's 16-bit form (h - min h clamped
+    to Ebar + 1); 16382 with unaries up to 4 Ebar makes the clamp bite.
+    16383 runs the 32-bit form."""
     from paper_1010_0012_gb300 import bp
-    rng = np.random.default_rng(10 * M + k)
+    rng = np.random.default_rng(10 * M + k + ebar)
     W, Hh = 9, 8
-    E = rng.integers(0, 30, (Hh, W, M)).astype(np.int32)
-    ebar = 40
+    E = rng.integers(0, 30 if ebar == 40 else 4 * ebar, (Hh, W, M)).astype(np.int32)
     pat = random_pattern(M, k, rng, integer=True, ebar=ebar)
     p0 = H.random_planes_min(W, Hh, M, rng)
+    if kernel == "registers":
+        # the schedule that runs is the one of the form Ebar selects
+        G = bp.BPGrid(W, Hh, M, bp.BP_I32)
+        bp.bp_set_potential_sparse(G.h, *pat, ebar, bp.BP_I32)
+        wf = bp.bp_get_sparse_kernel(G.h)[2]
+        G.close()
+        assert wf == bp.bp_sparse_schedule(M, pat[0], pat[1], 8 if ebar <= 16382 else 16)["wavefronts"]
     bel, mp, pl = _run(M, bp.BP_I32, p0, E, pat, ebar, 4, schedule, kernel)
     V = stereo.sparse_compatibility_matrix(pat[0], pat[1], pat[2].astype(np.int64), ebar, M, dtype=np.int64)
     p64, b64 = grid.grid_min_sum(E.astype(np.int64), V, 4, schedule, planes0=p0)
@@ -226,3 +236,4 @@ def test_kernel_choice_follows_the_pattern():
         bp.bp_set_sparse_kernel(G.h, bp.BP_SPARSE_REGISTERS)
     assert ei.value.status == bp.BP_ERR_UNSUPPORTED
     G.close()
+

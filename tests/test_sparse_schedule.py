@@ -9,17 +9,26 @@ Eq. 7 / Eq. 11 exactly, and what the reported cost means:
   * every label of the block is owned by exactly one lane of that block (so a
     store of a block stays inside one 128-byte line);
   * every lane runs LM steps, LM at least the longest list;
-  * the reported gather wavefronts per node are the sum, over blocks,
-    quarter-warps and steps, of the distinct slots read in the step's most-used
-    16-byte bank group (at least one)."""
+  * the reported gather wavefronts per node are the sum, over blocks, lane
+    sets and steps, of the distinct slots read in the step's most-used bank
+    group (at least one).
+Two gather shapes: 16-byte slots served to quarter-warps from eight 16-byte
+bank groups (FP32 / int32), and 8-byte slots served to half-warps from
+sixteen 8-byte groups (the 16-bit min-sum form)."""
 import numpy as np
 import pytest
 
 from paper_1010_0012_gb300 import bp
 
 
-def slot_of(x):
-    return (x & ~31) | ((x & 3) << 3) | ((x >> 2) & 7)
+def slot_of(x, gb):
+    if gb == 16:
+        return (x & ~31) | ((x & 3) << 3) | ((x >> 2) & 7)
+    return (x & ~63) | ((x & 3) << 4) | ((x >> 2) & 15)
+
+
+GATHERS = [16, 8]
+BOUND8 = 96   # measured 84 for this pattern
 
 
 def padded(M):
@@ -38,8 +47,9 @@ def random_pattern(M, rng, lens):
     return np.array(rowptr, np.int32), np.array(cols, np.int32)
 
 
-def check_schedule(M, rowptr, cols):
-    sch = bp.bp_sparse_schedule(M, rowptr, cols)
+def check_schedule(M, rowptr, cols, gb=16):
+    S, G = (8, 8) if gb == 16 else (16, 16)   # lanes per set, bank groups
+    sch = bp.bp_sparse_schedule(M, rowptr, cols, gb)
     assert sch is not None
     KM, LM, lab, ent = sch["KM"], sch["LM"], sch["lab"], sch["ent"]
     Mp = padded(M)
@@ -54,19 +64,19 @@ def check_schedule(M, rowptr, cols):
     seen = np.zeros(len(cols), np.int64)
     wavefronts = 0
     for k in range(KM):
-        for q in range(4):
+        for q in range(32 // S):
             for c in range(LM):
                 slots = set()
-                for l in range(8 * q, 8 * q + 8):
+                for l in range(S * q, S * q + S):
                     off, p = int(ent[k, c, l, 0]), int(ent[k, c, l, 1])
                     if off == 0xFFFF:
                         continue
                     x = int(lab[k, l])
                     assert 0 <= x < M and rowptr[x] <= p < rowptr[x + 1], "entry in a lane that does not own its row"
-                    assert off == 16 * slot_of(int(cols[p]))
+                    assert off == gb * slot_of(int(cols[p]), gb)
                     seen[p] += 1
-                    slots.add(off // 16)
-                per_group = np.bincount([s_ & 7 for s_ in slots], minlength=8)
+                    slots.add(off // gb)
+                per_group = np.bincount([s_ & (G - 1) for s_ in slots], minlength=G)
                 wavefronts += max(1, int(per_group.max()))
     assert np.all(seen == 1)
     assert sch["wavefronts"] == wavefronts
@@ -77,11 +87,14 @@ def check_schedule(M, rowptr, cols):
     return sch
 
 
-def test_benchmark_pattern_schedules_below_the_list_kernel():
+@pytest.mark.parametrize("gb", GATHERS)
+def test_benchmark_pattern_schedules_below_the_list_kernel(gb):
     """1280x720 workload's pattern: 9 random sender labels per receiver label,
     M = 128 (seed 7).  The list kernel's measured order costs about 1.66
     wavefronts per quarter-warp step, 36 steps x 4 quarter-warps = 239 per
-    node; nine steps per block must do well under that."""
+    node; nine steps per block must do well under that (16-byte slots: floor
+    4 blocks x 4 quarter-warps x 9 = 144).  8-byte slots: floor 4 x 2 x 9 = 72
+    wavefronts, each serving twice the lanes."""
     M = 128
     rng = np.random.default_rng(7)
     rowptr, cols = [0], []
@@ -90,27 +103,29 @@ def test_benchmark_pattern_schedules_below_the_list_kernel():
         rng.uniform(0.2, 1.0, 9)
         cols.extend(int(x) for x in xs)
         rowptr.append(len(cols))
-    sch = check_schedule(M, np.array(rowptr, np.int32), np.array(cols, np.int32))
-    assert sch["LM"] == 9 and sch["wavefronts"] <= 170
+    sch = check_schedule(M, np.array(rowptr, np.int32), np.array(cols, np.int32), gb)
+    assert sch["LM"] == 9 and sch["wavefronts"] <= (170 if gb == 16 else BOUND8)
 
 
+@pytest.mark.parametrize("gb", GATHERS)
 @pytest.mark.parametrize("M,seed", [(2, 0), (3, 1), (16, 2), (17, 3), (31, 4), (33, 5), (64, 6), (100, 7),
                                     (128, 8), (200, 9), (256, 10)])
-def test_random_patterns_of_uneven_rows(M, seed):
+def test_random_patterns_of_uneven_rows(M, seed, gb):
     rng = np.random.default_rng(seed)
     cap = {1: 40, 2: 20, 4: 10, 8: 5}[max(1, padded(M) // 32)]
     rowptr, cols = random_pattern(M, rng, lambda xj: rng.integers(0, min(cap, M) + 1))
-    check_schedule(M, rowptr, cols)
+    check_schedule(M, rowptr, cols, gb)
 
 
-def test_band_written_as_lists_and_empty_rows():
+@pytest.mark.parametrize("gb", GATHERS)
+def test_band_written_as_lists_and_empty_rows(gb):
     M, T = 128, 4
     rowptr, cols = [0], []
     for xj in range(M):
         cols.extend(x for x in range(max(0, xj - T), min(M, xj + T + 1)))
         rowptr.append(len(cols))
-    check_schedule(M, np.array(rowptr, np.int32), np.array(cols, np.int32))
-    check_schedule(64, np.zeros(65, np.int32), np.zeros(0, np.int32))
+    check_schedule(M, np.array(rowptr, np.int32), np.array(cols, np.int32), gb)
+    check_schedule(64, np.zeros(65, np.int32), np.zeros(0, np.int32), gb)
 
 
 def test_patterns_without_a_schedule():
@@ -127,3 +142,5 @@ def test_schedule_argument_errors():
         bp.bp_sparse_schedule(1, np.zeros(2, np.int32), np.zeros(0, np.int32))
     with pytest.raises(bp.BPError):
         bp.bp_sparse_schedule(4, np.array([0, 1, 1, 1, 1], np.int32), np.array([9], np.int32))
+    with pytest.raises(bp.BPError):
+        bp.bp_sparse_schedule(4, np.array([0, 1, 1, 1, 1], np.int32), np.array([2], np.int32), 4)

@@ -19,7 +19,7 @@ assert lib.bp_create(0, 4, 8, 0, None, ctypes.byref(out)) == 1
 rp = (ctypes.c_int32 * 5)(0, 1, 2, 2, 3)
 cl = (ctypes.c_int32 * 3)(1, 0, 3)
 v = [ctypes.c_int() for _ in range(4)]
-assert lib.bp_sparse_schedule(4, rp, cl, *[ctypes.byref(x) for x in v], None, None) == 0
+assert lib.bp_sparse_schedule(4, rp, cl, 16, *[ctypes.byref(x) for x in v], None, None) == 0
 """
 
 
