@@ -717,8 +717,8 @@ def gradient_floor_bytes(cfg, every=5):
 def measure_gradient(args, every=5):
     """Loss and gradient (alpha, fbar, beta) of 30 unrolled log-domain
     iterations on 256x256, M=64, T=3, checkpoint every 5.  Wall-clock time per
-    gradient (the call a user makes: forward, loss, backward, gradients read
-    back to the host), against the byte floor of its launches."""
+    gradient (the call a user makes: forward, loss, backward, the three
+    gradients read back to the host), against the byte floor of its launches."""
     import torch
     from paper_1010_0012_gb300 import autograd, bp
     cfg = wl.CONFIGS["grid256_m64_grad"]
@@ -730,15 +730,18 @@ def measure_gradient(args, every=5):
     # the handle orders its work on torch's stream: no host synchronisation
     # between the library's kernels and torch's
     G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_F32, stream=torch.cuda.current_stream())
-    beta0 = torch.tensor(cfg.beta, device="cuda")
+    # the parameters live on the GPU, as in a training loop: the reverse pass
+    # keeps their gradients on the device and the step waits once, when the
+    # three gradients are read back
+    a = torch.tensor(cfg.alpha, device="cuda", requires_grad=True)
+    fb = torch.tensor(float(np.exp(-cfg.alpha * cfg.T)), device="cuda", requires_grad=True)
+    be = torch.tensor(cfg.beta, device="cuda", requires_grad=True)
 
     def step():
-        a = torch.tensor(cfg.alpha, requires_grad=True)
-        fb = torch.tensor(float(np.exp(-cfg.alpha * cfg.T)), requires_grad=True)
-        be = beta0.clone().requires_grad_(True)
+        a.grad = fb.grad = be.grad = None
         loss = autograd.stereo_nll(cost, gt, a, fb, be, cfg.T, cfg.iters, G, every)
         loss.backward()
-        return float(a.grad)
+        return torch.stack([a.grad, fb.grad, be.grad]).cpu()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()

@@ -200,6 +200,14 @@ bp_status bp_set_messages(bp_handle h, const void *dev_planes);
 bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
                       double *host_dfbar);
 
+/* bp_backward with the parameter gradients in device memory: dev_dtable
+ * [2T + 1] and *dev_dfbar (float64, device) are written by copies on the
+ * handle's stream, like dev_dlogg, and nothing synchronises, so a caller can
+ * queue more work behind the reverse pass (no counterpart in the paper; the
+ * values equal bp_backward's bit for bit). */
+bp_status bp_backward_device(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *dev_dtable,
+                             double *dev_dfbar);
+
 /* Checkpoint interval used by BP_RECORD runs (default 5): the recorded run
  * keeps every `every`-th message state, and bp_backward recomputes the states
  * between them (no counterpart in the paper). */

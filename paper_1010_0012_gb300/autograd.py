@@ -6,6 +6,9 @@ BPFunction maps (log g, band table f(d), fbar) to the normalised log-beliefs
 after K unrolled synchronous sum-product iterations.  Its backward calls
 bp_backward, which recomputes each checkpoint segment and runs the adjoint
 kernel; the parameter gradients (dL/df(d), dL/dfbar) come back in FP64.
+With the table (and fbar) on the GPU the backward calls bp_backward_device:
+the gradients stay on the device and no host wait interrupts autograd, so
+the rest of the backward graph is queued while the reverse pass runs.
 The library does all of the BP arithmetic; this module only moves tensors.
 """
 from __future__ import annotations
@@ -23,7 +26,16 @@ class BPFunction(torch.autograd.Function):
             raise TypeError("logg must be a float32 CUDA tensor [H][W][M]")
         h = grid.h
         bp.bp_set_unary_log(h, logg.detach().contiguous())
-        bp.bp_set_potential(h, table.detach().cpu().numpy().astype(np.float32), T, float(fbar), bp.BP_F32)
+        if table.is_cuda:
+            # the library takes the table on the host: one copy for the table
+            # and fbar, in float64 so that both values arrive unchanged
+            fb = fbar.detach().reshape(1).to(device=table.device, dtype=torch.float64) \
+                if isinstance(fbar, torch.Tensor) else torch.tensor([float(fbar)], dtype=torch.float64, device=table.device)
+            vals = torch.cat([table.detach().reshape(-1).double(), fb]).cpu().numpy()
+            tab_h, fbar_h = vals[:-1].astype(np.float32), float(vals[-1])
+        else:
+            tab_h, fbar_h = table.detach().cpu().numpy().astype(np.float32), float(fbar)
+        bp.bp_set_potential(h, tab_h, T, fbar_h, bp.BP_F32)
         bp.bp_set_checkpoint_interval(h, every)
         bp.bp_reset_messages(h)
         bp.bp_iterate(h, n_iters, bp.BP_SUM | bp.BP_LOG | bp.BP_RECORD, bp.BP_SYNC)
@@ -34,18 +46,34 @@ class BPFunction(torch.autograd.Function):
         ctx.grid = grid
         ctx.T = T
         ctx.table_meta = (table.dtype, table.device)
-        ctx.fbar_meta = (fbar.dtype, fbar.device) if isinstance(fbar, torch.Tensor) else None
+        ctx.fbar_meta = (fbar.dtype, fbar.device, fbar.shape) if isinstance(fbar, torch.Tensor) else None
         return logb
 
     @staticmethod
     def backward(ctx, dlogb):
         dlogg = torch.empty_like(dlogb)
-        dtab, dfbar = bp.bp_backward(ctx.grid.h, dlogb.detach().float().contiguous(), dlogg, 2 * ctx.T + 1)
         tdt, tdev = ctx.table_meta
+        n = 2 * ctx.T + 1
+        h = ctx.grid.h
+        if tdev.type == "cuda" and (ctx.fbar_meta is None or ctx.fbar_meta[1].type == "cuda"):
+            # parameters on the GPU: the float64 gradients stay there and
+            # nothing waits for the reverse pass
+            dt = torch.empty(n, dtype=torch.float64, device=dlogb.device)
+            df = torch.empty(1, dtype=torch.float64, device=dlogb.device)
+            bp.bp_backward_device(h, dlogb.detach().float().contiguous(), dlogg, dt, df)
+            if not ctx.grid.on_current_stream():
+                bp.bp_sync(h)
+            g_tab = dt.to(device=tdev, dtype=tdt)
+            g_fbar = None
+            if ctx.fbar_meta is not None:
+                g_fbar = df.reshape(ctx.fbar_meta[2]).to(device=ctx.fbar_meta[1], dtype=ctx.fbar_meta[0])
+            return dlogg, g_tab, g_fbar, None, None, None, None
+        dtab, dfbar = bp.bp_backward(h, dlogb.detach().float().contiguous(), dlogg, n)
         g_tab = torch.as_tensor(dtab, dtype=torch.float64).to(device=tdev, dtype=tdt)
         g_fbar = None
         if ctx.fbar_meta is not None:
-            g_fbar = torch.tensor(dfbar, dtype=torch.float64).to(device=ctx.fbar_meta[1], dtype=ctx.fbar_meta[0])
+            g_fbar = torch.tensor(dfbar, dtype=torch.float64).reshape(ctx.fbar_meta[2]).to(
+                device=ctx.fbar_meta[1], dtype=ctx.fbar_meta[0])
         return dlogg, g_tab, g_fbar, None, None, None, None
 
 

@@ -54,6 +54,7 @@ def _load():
         "bp_get_messages": ([P, P], I),
         "bp_set_messages": ([P, P], I),
         "bp_backward": ([P, P, P, P, P], I),
+        "bp_backward_device": ([P, P, P, P, P], I),
         "bp_set_checkpoint_interval": ([P, I], I),
         "bp_set_persistent": ([P, I], I),
         "bp_set_sparse_kernel": ([P, I], I),
@@ -242,6 +243,13 @@ def bp_backward(h, dlogb: torch.Tensor, dlogg: torch.Tensor, n_table: int):
     _check(h, _lib.bp_backward(h, _dptr(dlogb, torch.float32), _dptr(dlogg, torch.float32),
                                dtab.ctypes.data_as(ctypes.c_void_p), ctypes.byref(dfbar)))
     return dtab, dfbar.value
+
+
+def bp_backward_device(h, dlogb: torch.Tensor, dlogg: torch.Tensor, dtab: torch.Tensor, dfbar: torch.Tensor):
+    """bp_backward with dL/df(d) and dL/dfbar written into float64 CUDA tensors
+    on the handle's stream (no synchronisation)."""
+    _check(h, _lib.bp_backward_device(h, _dptr(dlogb, torch.float32), _dptr(dlogg, torch.float32),
+                                      _dptr(dtab, torch.float64), _dptr(dfbar, torch.float64, 1)))
 
 
 def bp_set_checkpoint_interval(h, every):

@@ -116,22 +116,24 @@ bp_status bpg_record_forward(bp_ctx *h, int n_iters) {
     return BP_OK;
 }
 
-extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
-                                 double *host_dfbar) {
-    BPG_TRACE("bp_backward");
-    if (!h) return bpg_fail(nullptr, BP_ERR_ARG, "bp_backward: NULL handle");
+// The reverse pass of bp_backward / bp_backward_device.  dtable and dfbar
+// are host memory (written after a synchronisation of the handle's stream) or,
+// with device_out, device memory written by copies on that stream.
+static bp_status backward_impl(bp_ctx *h, const char *name, const float *dev_dlogb, float *dev_dlogg,
+                               double *dtable, double *dfbar, bool device_out) {
+    if (!h) return bpg_fail(nullptr, BP_ERR_ARG, std::string(name) + ": NULL handle");
     h->err.clear();
-    if (!dev_dlogb || !dev_dlogg || !host_dtable || !host_dfbar)
-        return bpg_fail(h, BP_ERR_ARG, "bp_backward: NULL argument");
+    if (!dev_dlogb || !dev_dlogg || !dtable || !dfbar)
+        return bpg_fail(h, BP_ERR_ARG, std::string(name) + ": NULL argument");
     if (!h->recorded || !h->msg_log)
-        return bpg_fail(h, BP_ERR_STATE, "bp_backward: run bp_iterate with BP_SUM|BP_LOG|BP_RECORD first");
-    if (!h->fast) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: needs T <= 8 and M <= 512");
+        return bpg_fail(h, BP_ERR_STATE, std::string(name) + ": run bp_iterate with BP_SUM|BP_LOG|BP_RECORD first");
+    if (!h->fast) return bpg_fail(h, BP_ERR_UNSUPPORTED, std::string(name) + ": needs T <= 8 and M <= 512");
     if (bp_status st = bpg_check_device(h)) return st;
     const int K = h->rec_iters, c = h->rec_every, Teff = h->Teff, NP = 2 * Teff + 2;
     const size_t sb = bpg_state_bytes(h);
     const long long nodes = (long long)h->W * h->H;
     const int blocks = adjoint_blocks(h->dims, h->adj_layout, Teff);
-    if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, "bp_backward: no adjoint kernel for this layout");
+    if (blocks < 1) return bpg_fail(h, BP_ERR_UNSUPPORTED, std::string(name) + ": no adjoint kernel for this layout");
     if (bp_status st = ensure_segment_buffer(h, c)) return st;
     if (bp_status st = bpg_ensure_buffer(h, &h->adj[0], sb, "adjoint state")) return st;
     if (bp_status st = bpg_ensure_buffer(h, &h->adj[1], sb, "adjoint state")) return st;
@@ -185,16 +187,41 @@ extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev
             ca ^= 1;
         }
     }
-    std::vector<double> red(NP, 0.0);
     if (rows > 0) {
         BK_CK(h, launch_reduce_partials_f64((const float *)h->dtab_partial, rows, NP, (double *)h->d_red, h->stream));
         h->launches += 1;
-        BK_CK(h, cudaMemcpyAsync(red.data(), h->d_red, NP * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    } else {
+        BK_CK(h, cudaMemsetAsync(h->d_red, 0, NP * sizeof(double), h->stream));
     }
     BK_CK(h, launch_unpad_copy(h->dlogg_pad, dev_dlogg, nodes, h->M, h->Mp, h->stream));
     h->launches += 1;
+    // d_red holds dL/df(d) for |d| <= Teff, then dL/dfbar; table entries with
+    // |d| > Teff (T >= M) meet no label pair and get 0
+    const int T = h->T;
+    if (device_out) {
+        if (T > Teff) BK_CK(h, cudaMemsetAsync(dtable, 0, (size_t)(2 * T + 1) * sizeof(double), h->stream));
+        BK_CK(h, cudaMemcpyAsync(dtable + (T - Teff), h->d_red, (size_t)(2 * Teff + 1) * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, h->stream));
+        BK_CK(h, cudaMemcpyAsync(dfbar, (const double *)h->d_red + (NP - 1), sizeof(double), cudaMemcpyDeviceToDevice,
+                                 h->stream));
+        return BP_OK;
+    }
+    std::vector<double> red(NP, 0.0);
+    BK_CK(h, cudaMemcpyAsync(red.data(), h->d_red, NP * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (bp_status st = bp_sync(h)) return st;
-    for (int d = -h->T; d <= h->T; ++d) host_dtable[d + h->T] = (d >= -Teff && d <= Teff) ? red[d + Teff] : 0.0;
-    *host_dfbar = red[NP - 1];
+    for (int d = -T; d <= T; ++d) dtable[d + T] = (d >= -Teff && d <= Teff) ? red[d + Teff] : 0.0;
+    *dfbar = red[NP - 1];
     return BP_OK;
+}
+
+extern "C" bp_status bp_backward(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *host_dtable,
+                                 double *host_dfbar) {
+    BPG_TRACE("bp_backward");
+    return backward_impl(h, "bp_backward", dev_dlogb, dev_dlogg, host_dtable, host_dfbar, false);
+}
+
+extern "C" bp_status bp_backward_device(bp_handle h, const float *dev_dlogb, float *dev_dlogg, double *dev_dtable,
+                                        double *dev_dfbar) {
+    BPG_TRACE("bp_backward_device");
+    return backward_impl(h, "bp_backward_device", dev_dlogb, dev_dlogg, dev_dtable, dev_dfbar, true);
 }

@@ -29,13 +29,14 @@ def test_log_forward_matches_oracle(M, T, schedule):
     H.check_sum_case(g, tab, T, fbar, 7, schedule, log=True)
 
 
-def _gpu_grad(cost, d_gt, alpha, fbar, beta, T, K, every, on_torch_stream=False):
+def _gpu_grad(cost, d_gt, alpha, fbar, beta, T, K, every, on_torch_stream=False, params_on_gpu=False):
     import torch
     from paper_1010_0012_gb300 import autograd, bp
     Hh, W, M = cost.shape
     G = bp.BPGrid(W, Hh, M, bp.BP_F32, stream=torch.cuda.current_stream() if on_torch_stream else None)
-    a = torch.tensor(alpha, dtype=torch.float32, requires_grad=True)
-    fb = torch.tensor(fbar, dtype=torch.float32, requires_grad=True)
+    pdev = "cuda" if params_on_gpu else "cpu"
+    a = torch.tensor(alpha, dtype=torch.float32, device=pdev, requires_grad=True)
+    fb = torch.tensor(fbar, dtype=torch.float32, device=pdev, requires_grad=True)
     b = torch.tensor(beta, dtype=torch.float32, device="cuda", requires_grad=True)
     cost_t = torch.from_numpy(np.ascontiguousarray(cost, dtype=np.float32)).cuda()
     loss = autograd.stereo_nll(cost_t, d_gt, a, fb, b, T, K, G, every)
@@ -147,3 +148,76 @@ def test_grid_on_torch_stream_gives_the_same_gradient():
     a = _gpu_grad(*args)
     b = _gpu_grad(*args, on_torch_stream=True)
     assert a == b
+
+
+def test_parameters_on_the_gpu_give_the_same_gradient():
+    """With the table f(d) and fbar on the GPU the backward takes the
+    device-output reverse pass (bp_backward_device: no host wait).  Given the
+    same parameter values, the gradients wrt log g, f(d) and fbar must equal
+    the host path's bit for bit, on the handle's own stream and on torch's."""
+    import dataclasses
+    import torch
+    from paper_1010_0012_gb300 import autograd, bp
+    cfg = dataclasses.replace(wl.CONFIGS["grid256_m64_grad"], W=48, H=40)
+    st = wl.make_stereo(cfg)
+    T, K = cfg.T, 12
+    logg0 = torch.from_numpy((-0.1 * st.cost).astype(np.float32)).cuda()
+    tab = np.exp(-0.9 * np.abs(np.arange(-T, T + 1))).astype(np.float32)
+    fbar = np.float32(np.exp(-0.9 * (T + 1)))
+    wts = torch.from_numpy(np.random.default_rng(3).standard_normal(logg0.shape).astype(np.float32)).cuda()
+    outs = []
+    for dev, torch_stream in (("cpu", False), ("cuda", False), ("cuda", True)):
+        G = bp.BPGrid(cfg.W, cfg.H, cfg.M, bp.BP_F32, stream=torch.cuda.current_stream() if torch_stream else None)
+        lg = logg0.clone().requires_grad_(True)
+        tab_t = torch.tensor(tab, device=dev, requires_grad=True)
+        fb_t = torch.tensor(fbar, device=dev, requires_grad=True)
+        logb = autograd.log_beliefs(lg, tab_t, fb_t, G, T, K, 4)
+        (logb * wts).sum().backward()
+        outs.append((lg.grad.cpu().numpy(), tab_t.grad.cpu().numpy(), float(fb_t.grad)))
+        G.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[0], outs[0][0])
+        np.testing.assert_array_equal(o[1], outs[0][1])
+        assert o[2] == outs[0][2]
+
+
+@pytest.mark.parametrize("M,T,K", [(16, 3, 7), (8, 9, 5), (16, 2, 0)])
+def test_backward_device_equals_backward(M, T, K):
+    """bp_backward_device writes the same float64 parameter gradients as
+    bp_backward, including the zero entries of |d| > M - 1 (T = 9 > 7) and a
+    recorded run of no iterations, and the same dL/d log g."""
+    import torch
+    from paper_1010_0012_gb300 import bp
+    rng = np.random.default_rng(M + T + K)
+    W, Hh = 9, 7
+    logg = torch.from_numpy(rng.uniform(-3.0, 0.0, (Hh, W, M)).astype(np.float32)).cuda()
+    tab = np.exp(-0.7 * np.abs(np.arange(-T, T + 1))).astype(np.float32)
+    fbar = float(np.float32(np.exp(-0.7 * (T + 1))))
+    dlogb = torch.from_numpy(rng.standard_normal((Hh, W, M)).astype(np.float32)).cuda()
+    outs = []
+    for device_out in (False, True):
+        G = bp.BPGrid(W, Hh, M, bp.BP_F32)
+        bp.bp_set_unary_log(G.h, logg)
+        bp.bp_set_potential(G.h, tab, T, fbar, bp.BP_F32)
+        bp.bp_set_checkpoint_interval(G.h, 3)
+        G.reset()
+        bp.bp_iterate(G.h, K, bp.BP_SUM | bp.BP_LOG | bp.BP_RECORD, bp.BP_SYNC)
+        logb = torch.empty_like(logg)
+        bp.bp_beliefs(G.h, logb)
+        dlogg = torch.empty_like(logg)
+        if device_out:
+            dt = torch.full((2 * T + 1,), 7.0, dtype=torch.float64, device="cuda")
+            df = torch.full((1,), 7.0, dtype=torch.float64, device="cuda")
+            bp.bp_backward_device(G.h, dlogb, dlogg, dt, df)
+            G.sync()
+            dtab, dfbar = dt.cpu().numpy(), float(df.cpu()[0])
+        else:
+            dtab, dfbar = bp.bp_backward(G.h, dlogb, dlogg, 2 * T + 1)
+        outs.append((np.asarray(dtab), dfbar, dlogg.cpu().numpy()))
+        G.close()
+    (t0, f0, g0), (t1, f1, g1) = outs
+    np.testing.assert_array_equal(t0, t1)
+    assert f0 == f1
+    np.testing.assert_array_equal(g0, g1)
+    if T > M - 1:
+        assert np.all(t1[:T - (M - 1)] == 0) and np.all(t1[T + M:] == 0)
