@@ -137,6 +137,7 @@ inline int f2v_chunks(int Mp) {
 struct FgTable {
     const int2 *ell;        // per slot: [rows_s][32 KM] entries
     const int32_t *meta;    // [3][KM][32][3]: entry count, foreign count, own label (-1: none)
+                            // (the kernel reads the last two: past its count a lane reads padding)
     long long base[3];      // start of slot s in ell
     int rows[3];            // steps of slot s
 };
@@ -173,31 +174,32 @@ __global__ void __launch_bounds__(kFgBlock) f2v_kernel(const E *n_vf, E *m_fv, c
             const E *nu = n + u * Mp, *nwv = n + w * Mp;
             const E flat = MIN ? fbar_or_ebar + red[u] + red[w] : fbar_or_ebar * red[u] * red[w];
             const int2 *ell = tab.ell + tab.base[s] + lane;
-            int cnt[KM], nx[KM], lab[KM];
+            int nx[KM], lab[KM];
             E acc[KM], accx[KM];
 #pragma unroll
             for (int k = 0; k < KM; ++k) {
                 const int32_t *mt = tab.meta + (((long long)s * KM + k) * 32 + lane) * 3;
-                cnt[k] = __ldg(mt);
                 nx[k] = __ldg(mt + 1);
                 lab[k] = __ldg(mt + 2);
                 acc[k] = MIN ? flat : E(0);
                 accx[k] = MIN ? E(kBig) : E(0);
             }
+            // every lane runs the slot's steps: past its own list it reads
+            // padding entries that change nothing, so the loads carry no
+            // per-lane bound and the unrolled steps keep several in flight
             const int rows = tab.rows[s];
+#pragma unroll 4
             for (int i = 0; i < rows; ++i) {
 #pragma unroll
                 for (int k = 0; k < KM; ++k) {
-                    if (i < cnt[k]) {
-                        const int2 e = __ldg(ell + (long long)i * (32 * KM) + 32 * k);
-                        const E gu = nu[e.x & 0xffff], gwv = nwv[e.x >> 16];
-                        if (i < nx[k]) {
-                            if (MIN) accx[k] = __viaddmin_s32(e.y, gu + gwv, accx[k]);
-                            else accx[k] = fmaf(__int_as_float(e.y), gu * gwv, accx[k]);
-                        } else {
-                            if (MIN) acc[k] = __viaddmin_s32(e.y, gu + gwv, acc[k]);
-                            else acc[k] = fmaf(__int_as_float(e.y), gu * gwv, acc[k]);
-                        }
+                    const int2 e = __ldg(ell + (long long)i * (32 * KM) + 32 * k);
+                    const E gu = nu[e.x & 0xffff], gwv = nwv[e.x >> 16];
+                    if (i < nx[k]) {
+                        if (MIN) accx[k] = __viaddmin_s32(e.y, gu + gwv, accx[k]);
+                        else accx[k] = fmaf(__int_as_float(e.y), gu * gwv, accx[k]);
+                    } else {
+                        if (MIN) acc[k] = __viaddmin_s32(e.y, gu + gwv, acc[k]);
+                        else acc[k] = fmaf(__int_as_float(e.y), gu * gwv, acc[k]);
                     }
                 }
             }
@@ -590,7 +592,11 @@ bp_status bp_fg_set_factor(bp_factor_graph g, int C, const int32_t *host_triplet
         base[s] = total;
         total += (long long)rows * L;
     }
-    std::vector<int2> ell((size_t)std::max(1LL, total), make_int2(0, 0));
+    // steps past a lane's list read an entry that changes nothing: labels 0
+    // and weight 0 (sum: adds 0) or E = Ebar (min-sum: never below the flat
+    // term Ebar + min n_u + min n_w), so the kernel needs no bound per lane
+    const int2 pad = make_int2(0, g->dtype == BP_F32 ? 0 : (int32_t)fbar);
+    std::vector<int2> ell((size_t)std::max(1LL, total), pad);
     for (int s = 0; s < 3; ++s)
         for (int k = 0; k < KM; ++k)
             for (int l = 0; l < 32; ++l) {
