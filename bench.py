@@ -825,10 +825,11 @@ def run_multiscale_workload(args):
     print(json.dumps(line))
 
 
-def run_sparse_workload(args):
+def measure_sparse(args):
     """The O(nnz) kernel on the 1280x720, M=128 grid with a potential that is
     not a function of x_i - x_j: 9 compatible sender labels per receiver label
-    drawn at random (seed 7) with random values; message updates/s."""
+    drawn at random (seed 7) with random values; message updates/s of the
+    register-pattern and the list kernels, sum-product and min-sum."""
     import torch
     from paper_1010_0012_gb300 import bp
     cfg = wl.CONFIGS["grid1280x720_m128"]
@@ -887,22 +888,27 @@ def run_sparse_workload(args):
                                 "clocks": clk.summary()}
         G.close()
         del u
+    return res, {"workload": f"{cfg.W}x{cfg.H}, M={cfg.M}, random non-difference pattern (9 sender labels per "
+                             "receiver label, seed 7), 10 synchronous iterations per step; no L2 flush: each "
+                             "iteration streams 4.2 GB"}
+
+
+def run_sparse_workload(args):
+    res, config = measure_sparse(args)
     line = {"metric": METRIC + " (general sparse compatibility, 9 pairs per label)",
-            "value": res["sum_f32"]["registers"].get("value", res["sum_f32"]["lists"].get("value")), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{cfg.W}x{cfg.H}, M={cfg.M}, random non-difference pattern, 10 synchronous "
-                                   "iterations"},
-            "modes": res}
+            "value": res["sum_f32"]["registers"].get("value", res["sum_f32"]["lists"].get("value")), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": config, "modes": res}
     print(json.dumps(line))
 
 
-def run_factor_workload(args):
+def measure_factor(args, with_dense=True):
     """Sec. 7's three-variable factors: a second-order smoothness model on a
     256x256 stereo grid with M=32 labels.  Every horizontal and vertical run of
     three pixels is a factor with f = exp(-alpha |x0 - 2 x1 + x2|) where the
     second difference is at most 1 (C = compatible triplets) and fbar =
     exp(-2 alpha) elsewhere.  Factor-to-variable message entries per second of
-    the O(C + M) update against the standard O(M^3) update."""
+    the O(C + M) update, and (with_dense) of the standard O(M^3) update."""
     import torch
     from paper_1010_0012_gb300 import bp
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -926,16 +932,21 @@ def run_factor_workload(args):
     bp.bp_fg_set_factor(G, trip, vals, fbar, bp.BP_F32)
     units = len(fs) * 3 * M
     res = {}
-    for name, fn, K in (("sparse_O(C+M)", bp.bp_fg_iterate, 10), ("dense_O(M^3)", bp.bp_fg_iterate_dense, 2)):
+    modes = (("sparse_O(C+M)", bp.bp_fg_iterate, 10),) + \
+        ((("dense_O(M^3)", bp.bp_fg_iterate_dense, 2),) if with_dense else ())
+    for name, fn, K in modes:
         def step():
             bp.bp_fg_reset_messages(G)
             fn(G, K, bp.BP_SUM)
-        step()
+        for _ in range(max(1, args.warmup)):
+            step()
         bp.bp_fg_sync(G)
-        t = _event_time(stream, step, args.steps)
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            clk.wait_ready()
+            t = _event_time(stream, step, args.steps)
         bp.bp_fg_sync(G)
         res[name] = {"value": units * K / t, "unit": "factor-to-variable message entries/s",
-                     "ms_per_iter": t * 1e3 / K}
+                     "ms_per_iter": t * 1e3 / K, "clocks": clk.summary()}
     bp.bp_fg_destroy(G)
     # roofline of the O(C + M) iteration: every triplet contributes one term to
     # each of the three messages of every factor (n_factors * 3 * C terms per
@@ -954,11 +965,18 @@ def run_factor_workload(args):
         "frac": terms / t_it / peak_terms, "terms_per_iteration": terms,
         "hbm_bytes_per_iteration": len(fs) * 6 * M * 4 + W * H * M * 4 * 2,
         "hbm_frac": (len(fs) * 6 * M * 4 + W * H * M * 4 * 2) / t_it / (peaks()["hbm_gbs"] * 1e9)}
+    if with_dense:
+        res["speedup"] = res["sparse_O(C+M)"]["value"] / res["dense_O(M^3)"]["value"]
+    return res, {"workload": f"256x256 grid, M={M}, {len(fs)} triplet factors, C={len(trip)} of M^3={M ** 3}, "
+                             "10 flooding iterations per step"}
+
+
+def run_factor_workload(args):
+    res, config = measure_factor(args)
     line = {"metric": "factor BP message entries/s, O(C) vs O(M^3) (three-variable factors)",
             "value": res["sparse_O(C+M)"]["value"], "unit": "entries/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"256x256 grid, M={M}, {len(fs)} triplet factors, C={len(trip)} of M^3={M ** 3}"},
-            "modes": res, "speedup": res["sparse_O(C+M)"]["value"] / res["dense_O(M^3)"]["value"]}
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": config, "modes": {k: v for k, v in res.items() if k != "speedup"}, "speedup": res["speedup"]}
     print(json.dumps(line))
 
 
@@ -1055,8 +1073,10 @@ def main():
     if not args.no_secondary and world == 1:
         # the other workloads of the hot path, each with its own roofline and
         # clocks: the 384x288 red-black grid (both modes), the 64-MRF batch
-        # (both modes), the checkpointed gradient, and the O(mM) update
-        # against the tensor-core O(M^2) update at 256 labels
+        # (both modes), the checkpointed gradient, the O(mM) update against
+        # the tensor-core O(M^2) update at 256 labels, the general sparse
+        # potential (both kernels, both modes) and the three-variable factor
+        # graph (the O(C + M) update; its O(M^3) comparison only in its own run)
         sec_args = argparse.Namespace(**vars(args))
         sec_args.steps, sec_args.warmup = max(3, min(args.steps, 10)), max(3, min(args.warmup, 3))
         sec = {}
@@ -1066,7 +1086,9 @@ def main():
                         ("dense_compare_m256", lambda: (measure_dense_compare(sec_args, ((256, 4),), cuda_core=False),
                                                         {"workload": "1280x720, M = 256, T = 4, synchronous "
                                                                      "sum-product: O(mM) band against the fused and "
-                                                                     "packed BF16 tcgen05 O(M^2) updates"}))):
+                                                                     "packed BF16 tcgen05 O(M^2) updates"})),
+                        ("sparse1280x720", lambda: measure_sparse(sec_args)),
+                        ("factor256", lambda: measure_factor(sec_args, with_dense=False))):
             try:
                 r, c = fn()
                 sec[key] = {"config": c, "steps": sec_args.steps, "warmup": sec_args.warmup, "result": r}
