@@ -101,6 +101,19 @@ class _NegScaledCost(torch.autograd.Function):
         return None, g.to(device=beta.device, dtype=beta.dtype)
 
 
+_OFFSETS = {}
+
+
+def _neg_abs_offsets(T, device):
+    """-|d| for d = -T..T as float32 on `device`, made once per (T, device)."""
+    key = (int(T), str(device))
+    t = _OFFSETS.get(key)
+    if t is None:
+        t = -torch.arange(-T, T + 1, dtype=torch.float32, device=device).abs()
+        _OFFSETS[key] = t
+    return t
+
+
 def stereo_nll(cost, d_gt, alpha, fbar, beta, T, n_iters, grid, every=5):
     """-sum_i log b_i(x_i*) of the stereo model (Sec. 6) with parameters
     alpha, fbar, beta as tensors: log g = -beta cost, f(d) = exp(-alpha |d|)
@@ -110,8 +123,8 @@ def stereo_nll(cost, d_gt, alpha, fbar, beta, T, n_iters, grid, every=5):
     # the chain rule to beta sums dL/d log g * cost over every node: that
     # reduction stays in FP64 (the library's log g is FP32)
     logg = _NegScaledCost.apply(cost.float().contiguous(), beta)
-    d = torch.arange(-T, T + 1, dtype=torch.float32, device=alpha.device).abs()
-    table = torch.exp(-alpha * d)
+    # alpha * (-|d|) is -alpha * |d| exactly (IEEE products are sign-symmetric)
+    table = torch.exp(alpha * _neg_abs_offsets(T, alpha.device))
     logb = log_beliefs(logg, table, fbar, grid, T, n_iters, every)
     idx = torch.as_tensor(d_gt, dtype=torch.long, device=dev)[..., None]
     return -torch.gather(logb, -1, idx).sum()
