@@ -78,11 +78,25 @@ __global__ void __launch_bounds__(256, 4) v2f_kernel(const E *unary, const int32
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long v = warp; v < d.n_vars; v += nw) {
-        const int p0 = var_ptr[v], deg = var_ptr[v + 1] - p0;
-        int inc[D];
+    // A variable costs three dependent round trips: its row bounds, its
+    // incidence list, its messages.  The walk loads the row bounds two steps
+    // ahead and the incidence list one step ahead, so only the messages wait.
+    long long v = warp;
+    int deg = 0, p1 = 0, deg1 = 0;
+    int inc[D];
+    {
+        int p0 = 0;
+        if (v < d.n_vars) { p0 = var_ptr[v]; deg = var_ptr[v + 1] - p0; }
+        if (v + nw < d.n_vars) { p1 = var_ptr[v + nw]; deg1 = var_ptr[v + nw + 1] - p1; }
 #pragma unroll
         for (int j = 0; j < D; ++j) inc[j] = j < deg ? var_inc[p0 + j] : 0;
+    }
+    for (; v < d.n_vars; v += nw) {
+        int p2 = 0, deg2 = 0;
+        if (v + 2 * nw < d.n_vars) { p2 = var_ptr[v + 2 * nw]; deg2 = var_ptr[v + 2 * nw + 1] - p2; }
+        int incn[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) incn[j] = j < deg1 ? var_inc[p1 + j] : 0;
         E acc[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) acc[k] = MIN ? E(kBig) : E(0);
@@ -114,6 +128,11 @@ __global__ void __launch_bounds__(256, 4) v2f_kernel(const E *unary, const int32
                 n_vf[(long long)inc[k] * d.Mp + x] = o;
             }
         }
+#pragma unroll
+        for (int j = 0; j < D; ++j) inc[j] = incn[j];
+        deg = deg1;
+        p1 = p2;
+        deg1 = deg2;
     }
 }
 
