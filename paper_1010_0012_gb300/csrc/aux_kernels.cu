@@ -265,19 +265,53 @@ __global__ void beliefs_i32_kernel(const int32_t *e, const int32_t *planes, Grid
 }
 
 // ---- layout helpers ----------------------------------------------------------
+// transform of one value: 0 copy, 1 log, 2 exp, 3 natural log -> base-2 log
+__device__ __forceinline__ float pad_transform(float v, int lg) {
+    if (lg == 1) return logf(v);
+    if (lg == 2) return expf(v);
+    if (lg == 3) return v * 1.44269504088896341f;
+    return v;
+}
+
 __global__ void pad_f32_kernel(const float *src, float *dst, long long nodes, int M, int Mp, int lg) {
     const long long n = nodes * Mp;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const long long node = i / Mp;
         const int x = (int)(i - node * Mp);
-        float v = 0.f;
-        if (x < M) {
-            v = src[node * M + x];
-            if (lg == 1) v = logf(v);
-            else if (lg == 2) v = expf(v);
-            else if (lg == 3) v *= 1.44269504088896341f;   // natural log -> base-2 log
-        }
-        dst[i] = v;
+        dst[i] = x < M ? pad_transform(src[node * M + x], lg) : 0.f;
+    }
+}
+
+// M == Mp and 16-byte aligned buffers: the same values, 16 bytes per thread
+// and step, no index division
+__global__ void pad_f32_vec_kernel(const float4 *src, float4 *dst, long long n4, int lg) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = src[i];
+        dst[i] = make_float4(pad_transform(v.x, lg), pad_transform(v.y, lg), pad_transform(v.z, lg),
+                             pad_transform(v.w, lg));
+    }
+}
+
+// log g into the handle in one read: base-2 log g (transform 3) and g
+// (transform 2), each value as the two single passes compute it
+__global__ void log_unary_kernel(const float *src, float *dst_log2, float *dst_lin, long long nodes, int M, int Mp) {
+    const long long n = nodes * Mp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long node = i / Mp;
+        const int x = (int)(i - node * Mp);
+        const float v = x < M ? src[node * M + x] : 0.f;
+        dst_log2[i] = x < M ? pad_transform(v, 3) : 0.f;
+        dst_lin[i] = x < M ? pad_transform(v, 2) : 0.f;
+    }
+}
+
+__global__ void log_unary_vec_kernel(const float4 *src, float4 *dst_log2, float4 *dst_lin, long long n4) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+        const float4 v = src[i];
+        dst_log2[i] = make_float4(pad_transform(v.x, 3), pad_transform(v.y, 3), pad_transform(v.z, 3),
+                                  pad_transform(v.w, 3));
+        dst_lin[i] = make_float4(pad_transform(v.x, 2), pad_transform(v.y, 2), pad_transform(v.z, 2),
+                                 pad_transform(v.w, 2));
     }
 }
 
@@ -409,9 +443,27 @@ cudaError_t launch_dense_min(const DenseArgsI &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
 cudaError_t launch_pad_copy_f32(const float *src, float *dst, long long nodes, int M, int Mp, int log_transform,
                                 cudaStream_t s) {
-    pad_f32_kernel<<<grid_for(nodes * Mp, 256), 256, 0, s>>>(src, dst, nodes, M, Mp, log_transform);
+    const long long n = nodes * Mp;
+    if (M == Mp && (n & 3) == 0 && aligned16(src) && aligned16(dst))
+        pad_f32_vec_kernel<<<grid_for(n / 4, 256), 256, 0, s>>>((const float4 *)src, (float4 *)dst, n / 4,
+                                                                 log_transform);
+    else
+        pad_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst, nodes, M, Mp, log_transform);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_log_unary(const float *src, float *dst_log2, float *dst_lin, long long nodes, int M, int Mp,
+                             cudaStream_t s) {
+    const long long n = nodes * Mp;
+    if (M == Mp && (n & 3) == 0 && aligned16(src) && aligned16(dst_log2) && aligned16(dst_lin))
+        log_unary_vec_kernel<<<grid_for(n / 4, 256), 256, 0, s>>>((const float4 *)src, (float4 *)dst_log2,
+                                                                   (float4 *)dst_lin, n / 4);
+    else
+        log_unary_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst_log2, dst_lin, nodes, M, Mp);
     return cudaGetLastError();
 }
 

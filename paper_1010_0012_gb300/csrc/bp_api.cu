@@ -481,9 +481,9 @@ bp_status bp_set_unary_log(bp_handle h, const float *dev_logg) {
     if (bp_status st = bpg_check_device(h)) return st;
     const long long nodes = (long long)h->W * h->H;
     if (bp_status st = ensure_buffer(h, (void **)&h->log_unary, (size_t)nodes * h->Mp * 4, "log unary")) return st;
-    BP_CK(h, launch_pad_copy_f32(dev_logg, h->log_unary, nodes, h->M, h->Mp, 3, h->stream));   // to base 2
-    BP_CK(h, launch_pad_copy_f32(dev_logg, (float *)h->unary, nodes, h->M, h->Mp, 2, h->stream));
-    h->launches += 2;
+    // base-2 log g for the log-domain kernels and g for the linear ones
+    BP_CK(h, launch_log_unary(dev_logg, h->log_unary, (float *)h->unary, nodes, h->M, h->Mp, h->stream));
+    h->launches += 1;
     h->have_unary = true;
     h->log_unary_valid = true;
     h->recorded = false;

@@ -126,9 +126,12 @@ cudaError_t launch_unary_stereo_i32(const uint8_t *left, const uint8_t *right, i
                                     int Mp, int Tu, const int32_t *host_table, cudaStream_t s);
 
 // Utility kernels (aux_kernels.cu).
-// transform: 0 copy, 1 log, 2 exp
+// transform: 0 copy, 1 log, 2 exp, 3 natural log -> base-2 log
 cudaError_t launch_pad_copy_f32(const float *src, float *dst, long long nodes, int M, int Mp,
                                 int transform, cudaStream_t s);
+// natural log g -> padded base-2 log g and padded g, in one pass
+cudaError_t launch_log_unary(const float *src, float *dst_log2, float *dst_lin, long long nodes, int M, int Mp,
+                             cudaStream_t s);
 cudaError_t launch_pad_copy_i32(const int32_t *src, int32_t *dst, long long nodes, int M, int Mp,
                                 cudaStream_t s);
 cudaError_t launch_unpad_copy(const void *src, void *dst, long long rows, int M, int Mp,
